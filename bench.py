@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the batched direct-SCF JK build on GB300.
+
+Workload (one "step"): J and K of 64 independent seeded molecules of 10-60
+atoms (2:1 light:heavy, 6-31G*-shaped Cartesian basis, about 20,000 basis
+functions in all), one density each, cutoff 1e-13, all-FP64, every molecule
+in the same per-class persistent integral kernels. A step runs the whole
+per-iteration path: density block maxima, fused screening + Rys integrals +
+contraction with D + atomics (every class pair), symmetrisation of J and K.
+Basis setup (pair tables, Schwarz factors) is per geometry and reported as
+init_ms, outside the steps.
+
+Metric: significant shell quartets per second (whole job), plus ms per
+step. The L2 (129 MB) is flushed before every step by writing a 256 MiB
+buffer. Under torchrun each rank builds its own batch of 64 molecules
+(weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle (plain FP64 McMurchie-Davidson) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "JK build ms & quartets/s vs plain FP64 at max|ΔK|≤1e-8; % of FP32/FP64 peak"
+UNIT = "quartets/s"
+WORKLOAD = "batched-631gs-64mol"
+# GB300 FP64: 152 SMs x 4 FLOP/clk/SM (2 FP64 FMA) x 2.07 GHz ~= 1.26 TFLOP/s,
+# the 1.25 TFLOP/s nominal figure; FP32: 152 x 256 FLOP/clk x 2.07 GHz.
+PEAK_FP64_NOMINAL = 152 * 4 * 2.07e9
+PEAK_FP32_NOMINAL = 152 * 256 * 2.07e9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nmol", type=int, default=64)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
+    ap.add_argument("--cutoff", type=float, default=1e-13)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(mols, seconds: float, cutoff: float):
+    """Oracle (as it stands) on the smallest molecules until `seconds` pass."""
+    import oracle
+    order = sorted(range(len(mols)), key=lambda i: mols[i].natm)
+    nq = 0
+    t_total = 0.0
+    used = []
+    for i in order:
+        t0 = time.perf_counter()
+        _, _, n = oracle.jk(mols[i], cutoff=cutoff)
+        t_total += time.perf_counter() - t0
+        nq += n
+        used.append(mols[i].natm)
+        if t_total >= seconds:
+            break
+    return {"value": nq / t_total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"full screened FP64 JK of the {len(used)} smallest molecules of the batch "
+                      f"({min(used)}-{max(used)} atoms, {nq} quartets, {t_total:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2507_09772_gb300 import synth
+    import oracle
+    mols = synth.batched_631gs(args.nmol)
+    smallest = min(range(len(mols)), key=lambda i: mols[i].natm)
+    mol = mols[smallest]
+    for _ in range(args.warmup):
+        oracle.jk(mol, cutoff=args.cutoff)
+    t0 = time.perf_counter()
+    nq = 0
+    for _ in range(args.steps):
+        _, _, n = oracle.jk(mol, cutoff=args.cutoff)
+        nq += n
+    dt = time.perf_counter() - t0
+    val = nq / dt
+    sample = (f"each step: full screened FP64 JK of the smallest molecule of the batch "
+              f"({mol.natm} atoms, {mol.nao} functions, {nq // max(1, args.steps)} quartets)")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "nmol": args.nmol, "precision": "fp64",
+                                           "cutoff": args.cutoff, "sample": "smallest molecule"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2507_09772_gb300 import jk, synth
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    jk.load_library()
+    mols = synth.batched_631gs(args.nmol, seed_base=1001 + rank * 1000)
+    t0 = time.perf_counter()
+    eng = jk.JK(mols)
+    init_s = time.perf_counter() - t0
+    Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
+    Js = [torch.empty_like(d) for d in Ds]
+    Ks = [torch.empty_like(d) for d in Ds]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(stats=True):
+        flush.fill_(1)
+        _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=args.precision, J=Js, K=Ks, stats=stats)
+        return st
+
+    t0 = time.perf_counter()
+    first = step()
+    first_s = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    eng.set_option("profile", 1)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    prof = {}
+    for _ in range(args.steps):
+        st = step()
+        stats.append(st)
+        for p in jk.jk_profile(eng.h):
+            key = (p["la"], p["lb"], p["lc"], p["ld"], p["na"], p["nb"], p["nc"], p["nd"], p["tier"])
+            agg = prof.setdefault(key, dict(p, ms=0.0, flops_model=0.0, quartets=0, launches=0))
+            agg["ms"] += p["ms"]
+            agg["flops_model"] += p["flops_model"]
+            agg["quartets"] += p["quartets"]
+            agg["launches"] += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    eng.set_option("profile", 0)
+    quartets = sum(s["quartets_fp64"] + s["quartets_fp32"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+    ms_t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    q_t = torch.tensor([float(quartets)], dtype=torch.float64, device="cuda")
+    if pg:
+        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
+        pg.all_reduce(q_t, op=pg.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    value = float(q_t.item()) / (ms_max * 1e-3)
+
+    # dominant integral kernel and its roofline (FP64 or FP32 FMA pipe)
+    total_kernel_ms = sum(v["ms"] for v in prof.values())
+    dom = max(prof.values(), key=lambda v: v["ms"])
+    dom_ms = dom["ms"] / dom["launches"]
+    dom_flops = dom["flops_model"] / dom["launches"]
+    peak = PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL
+    probe = jk.jk_measure_peak("fp64" if dom["tier"] == 0 else "fp32", 100.0)
+    roofline = {
+        "bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+        "frac": dom_flops / (dom_ms * 1e-3) / peak, "traffic": None,
+        "kernel": "jk_class_kernel<(%d%d|%d%d) prims %d%d%d%d, %s>" % (
+            dom["la"], dom["lb"], dom["lc"], dom["ld"], dom["na"], dom["nb"], dom["nc"], dom["nd"],
+            "fp64" if dom["tier"] == 0 else "fp32"),
+        "kernel_share": dom["ms"] / ms_total,
+        "peak_source": "nominal FP64 FMA rate: 152 SMs x 4 FLOP/clk x 2.07 GHz" if dom["tier"] == 0
+        else "nominal FP32 FMA rate: 152 SMs x 256 FLOP/clk x 2.07 GHz",
+        "peak_probe_tflops": probe / 1e12, "frac_of_probe": dom_flops / (dom_ms * 1e-3) / probe,
+        "threads_per_quartet": dom["threads_per_quartet"], "regs": dom["regs"], "local_bytes": dom["local_bytes"],
+    }
+    all_flops = sum(v["flops_model"] for v in prof.values())
+    path_fp64 = {"model_tflops": all_flops / (total_kernel_ms * 1e-3) / 1e12,
+                 "frac_of_fp64_peak": all_flops / (total_kernel_ms * 1e-3) / PEAK_FP64_NOMINAL}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        Dh = [torch.tensor(m.D, dtype=torch.float64).pin_memory() for m in mols]
+        Jh = [torch.empty(d.shape, dtype=torch.float64).pin_memory() for d in Dh]
+        Kh = [torch.empty(d.shape, dtype=torch.float64).pin_memory() for d in Dh]
+        h2d = sum(d.numel() * 8 for d in Dh)
+        d2h = sum(j.numel() * 8 for j in Jh) + sum(k.numel() * 8 for k in Kh)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        nq = 0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            for d, dh in zip(Ds, Dh):
+                d.copy_(dh, non_blocking=True)
+            _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=args.precision, J=Js, K=Ks, stats=True)
+            nq += st["quartets_fp64"] + st["quartets_fp32"]
+            for j, jh in zip(Js, Jh):
+                jh.copy_(j, non_blocking=True)
+            for k, kh in zip(Ks, Kh):
+                kh.copy_(k, non_blocking=True)
+            torch.cuda.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
+        t_e = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+        n_e = torch.tensor([float(nq)], dtype=torch.float64, device="cuda")
+        if pg:
+            pg.all_reduce(t_e, op=pg.ReduceOp.MAX)
+            pg.all_reduce(n_e, op=pg.ReduceOp.SUM)
+        e2e = {"value": float(n_e.item()) / (float(t_e.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": float(t_e.item()) / args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample(mols, args.cpu_seconds, args.cutoff)
+
+    if rank == 0:
+        nbf = sum(m.nao for m in mols)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nmol": args.nmol, "nbf_total": nbf,
+                       "natm_range": [min(m.natm for m in mols), max(m.natm for m in mols)],
+                       "precision": args.precision, "cutoff": args.cutoff,
+                       "l2": "flushed before every step (256 MiB write)",
+                       "parallelism": f"{ws} independent batch(es), one per GPU"},
+            "quartets_per_step": quartets / args.steps,
+            "prim_quartets_per_step": sum(s["prim_quartets"] for s in stats) / args.steps,
+            "model_flops_per_step": sum(s["flops_model"] for s in stats) / args.steps,
+            "path_fp64_roofline": path_fp64,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+            "init_ms": 1e3 * init_s,
+            "first_build_s": first_s,
+            "compile_ms": eng.get_option("compile_ms"),
+            "peak_probe_fp64_tflops": jk.jk_measure_peak("fp64", 100.0) / 1e12,
+            "peak_probe_fp32_tflops": jk.jk_measure_peak("fp32", 100.0) / 1e12,
+            "top_kernels": sorted(
+                [{"class": "(%d%d|%d%d)/%d%d%d%d" % (v["la"], v["lb"], v["lc"], v["ld"], v["na"], v["nb"], v["nc"], v["nd"]),
+                  "tier": v["tier"], "ms_per_step": v["ms"] / args.steps, "share": v["ms"] / ms_total,
+                  "quartets_per_step": v["quartets"] / args.steps,
+                  "tflops_model": v["flops_model"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0,
+                  "G": v["threads_per_quartet"], "regs": v["regs"], "local_bytes": v["local_bytes"]}
+                 for v in prof.values()], key=lambda x: -x["ms_per_step"])[:12],
+        }
+        print(json.dumps(out))
+    eng.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * jk.h -- C ABI of the GB300 direct-SCF Coulomb/exchange (JK) build.
+ *
+ * Computes, for one or more densities D (Sec. 2, eq:jk of the paper),
+ *     J_ij = sum_kl (ij|kl) D_kl          K_ik = sum_jl (ij|kl) D_jl
+ * over contracted Gaussian-type-orbital shells (eq:rys0), with the electron
+ * repulsion integrals evaluated by Rys quadrature (eq:rys1, eq:rys2) on the
+ * GPU, shell quartets screened by the Schwarz inequality (eq:schwartz) times
+ * the largest density element they touch, and the 8-fold permutational
+ * symmetry of Sec. 2 (each unique quartet updates two J and four K blocks).
+ *
+ * Conventions
+ *   - Coordinates in bohr; a shell is (atom, l, nprim, prim_off, ao_off,
+ *     spherical). Cartesian components are ordered x exponent descending,
+ *     then y descending (xx, xy, xz, yy, yz, zz), the order of Sec. 2.
+ *   - coeffs[prim_off+i] multiplies the unnormalised primitive
+ *     x^lx y^ly z^lz exp(-exps[prim_off+i] r^2): normalisation is folded in
+ *     by the caller.
+ *   - spherical == 1 shells use real solid harmonics (m = -l..l; p stays
+ *     x, y, z). D is then given and J, K returned in that basis; the
+ *     Cartesian transform runs on the device (the paper does it outside the
+ *     integral kernel, Sec. 2).
+ *   - D, J, K: device pointers, n_dm x nao x nao, FP64, row major. D must
+ *     be symmetric (the symmetry of Sec. 2 assumes it). J and K are
+ *     overwritten. A NULL J (K) is allowed when with_j (with_k) is 0.
+ *
+ * Ownership and streams
+ *   - jk_init copies the basis to the device and owns every device buffer it
+ *     makes (pair tables, screening tables, scratch) until jk_destroy.
+ *   - The caller owns D, J, K and the CUDA stream. jk_build enqueues its
+ *     work on `stream` (NULL = legacy default stream) and returns without
+ *     synchronising, unless `stats` is non-NULL: then it synchronises the
+ *     stream to fill the counters and to check the device error word.
+ *   - A handle is not thread-safe: one build at a time per handle.
+ *
+ * Errors
+ *   Every call returns JK_OK or an error code; jk_last_error() gives a
+ *   message for the calling thread. No call aborts the process, traps on the
+ *   GPU or throws across the ABI. Device-side waits are bounded and report
+ *   JK_ERR_TIMEOUT through the device error word.
+ */
+#ifndef JK_H
+#define JK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    JK_OK = 0,
+    JK_ERR_ARG = 1,          /* bad argument (NULL pointer, size, flag) */
+    JK_ERR_UNSUPPORTED = 2,  /* l > JK_LMAX, nprim > JK_NPRIM_MAX, n_dm > JK_NDM_MAX */
+    JK_ERR_CUDA = 3,         /* a CUDA runtime or driver call failed */
+    JK_ERR_OOM = 4,          /* device allocation failed or above the memory cap */
+    JK_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+    JK_ERR_NAN = 6,          /* non-finite density or result detected */
+    JK_ERR_COMPILE = 7       /* runtime kernel compilation failed */
+};
+
+enum {
+    JK_PREC_FP64 = 0,          /* every quartet in FP64 */
+    JK_PREC_MIXED = 1,         /* Schwarz x density-max tiering: FP64 above tau32, FP32 below */
+    JK_PREC_MIXED_ROUTED = 2,  /* MIXED plus the learned router inside (tau32, K*tau32] */
+    JK_PREC_FP32 = 3           /* every quartet in FP32 (FP64 accumulation of J/K) */
+};
+
+#define JK_LMAX 4
+#define JK_NPRIM_MAX 16
+#define JK_NDM_MAX 4
+
+typedef struct {
+    int32_t atom, l, nprim, prim_off, ao_off, spherical;
+} jk_shell;
+
+typedef struct {
+    int64_t quartets_fp64;    /* significant unique shell quartets evaluated in FP64 */
+    int64_t quartets_fp32;    /* ... in FP32 */
+    int64_t quartets_routed;  /* band quartets the router moved to FP32 (part of quartets_fp32) */
+    int64_t prim_quartets;    /* primitive quartets evaluated (both tiers) */
+    double flops_model;       /* modelled FLOPs of the integral kernels (per-class count model) */
+    double ms;                /* device time of the build, CUDA events on `stream` */
+    int64_t kernel_launches;  /* kernels this build launched (integral + helper kernels) */
+} jk_stats;
+
+/* Per-launch record of the last build made with option "profile" = 1. */
+typedef struct {
+    int32_t la, lb, lc, ld, na, nb, nc, nd;  /* class: angular momenta, primitive counts */
+    int32_t tier;                            /* 0 FP64, 1 FP32 */
+    int32_t threads_per_quartet;             /* fragmentation (1 = one quartet per thread) */
+    int32_t regs, local_bytes;               /* registers per thread, local (spill) bytes */
+    int64_t quartets, prim_quartets;         /* significant quartets it evaluated */
+    double ms;                               /* CUDA-event time of the launch on the build stream */
+    double flops_model;                      /* modelled FLOPs of those quartets */
+} jk_launch_prof;
+
+typedef struct jk_handle jk_handle;
+
+/* One molecule. shells: nshell records (host); coords: natm x 3 (host,
+ * bohr); exps, coeffs: nprim_total (host). On success *out owns a new
+ * handle. Errors: JK_ERR_ARG (NULL, negative sizes, shell fields out of
+ * range), JK_ERR_UNSUPPORTED (l or nprim above the limits), JK_ERR_CUDA,
+ * JK_ERR_OOM, JK_ERR_COMPILE. */
+int jk_init(const jk_shell *shells, int32_t nshell, const double *coords, int32_t natm,
+            const double *exps, const double *coeffs, int32_t nprim_total, jk_handle **out);
+
+/* Several independent molecules in one handle (batched builds). Molecule m
+ * owns shells [mol_shell_off[m], mol_shell_off[m+1]); shell atom indices are
+ * global into coords, prim_off global into exps/coeffs, ao_off local to the
+ * molecule. */
+int jk_init_batch(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells,
+                  int32_t nshell, const double *coords, int32_t natm, const double *exps,
+                  const double *coeffs, int32_t nprim_total, jk_handle **out);
+
+/* J and K for a single-molecule handle (see the conventions above).
+ * cutoff: quartets with Q_ab Q_cd Dmax <= cutoff are skipped (the paper uses
+ * 1e-13). precision_mode: JK_PREC_*. stats may be NULL. */
+int jk_build(jk_handle *h, const double *D, int32_t n_dm, int with_j, int with_k, double cutoff,
+             int precision_mode, double *J, double *K, void *stream, jk_stats *stats);
+
+/* Batched build: D[m], J[m], K[m] are host arrays of nmol device pointers,
+ * one per molecule of the handle; every molecule is processed by the same
+ * per-class persistent kernels, captured once into a CUDA graph and
+ * replayed on later calls with the same flags. */
+int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_j, int with_k,
+                   double cutoff, int precision_mode, double *const *J, double *const *K,
+                   void *stream, jk_stats *stats);
+
+/* Options (double-valued): "tau32" (FP32 tier threshold on Q_ab Q_cd Dmax,
+ * default 1e-7), "router_band" (K, default 100), "pair_cutoff" (shell pairs
+ * with Q_ab at or below it are dropped at init, default 1e-18),
+ * "use_graph" (0/1), "use_dmax" (0/1: 0 screens with Dmax := 1),
+ * "profile" (0/1: CUDA events around every integral launch, see jk_profile).
+ * JK_ERR_ARG for an unknown key. */
+int jk_set_option(jk_handle *h, const char *key, double value);
+int jk_get_option(jk_handle *h, const char *key, double *value);
+
+/* Number of molecules, basis functions of molecule m (in the basis D is
+ * given in), shells. */
+int jk_info(jk_handle *h, int32_t mol, int32_t *nao, int32_t *nshell, int32_t *nmol);
+
+/* Schwarz factors Q_ab of molecule 0 into a host nshell x nshell array
+ * (zero for pairs dropped at init). */
+int jk_schwarz(jk_handle *h, double *Q_host);
+
+int jk_destroy(jk_handle *h);
+
+/* After a build with option "profile" = 1 and non-NULL stats: copies up to
+ * `max` launch records into out and their count into *n. */
+int jk_profile(jk_handle *h, jk_launch_prof *out, int32_t max, int32_t *n);
+
+/* FMA-chain throughput of the current device, FLOP/s (FMA = 2):
+ * which = 0 FP64, 1 FP32. Runs for about `ms` milliseconds. */
+int jk_measure_peak(int32_t which, double ms, double *flops_per_s);
+
+/* Ahead-of-time compilation of one class kernel (angular momenta la..ld,
+ * primitive counts na..nd, n_dm, flags, fp32 = 1 for the FP32 tier) into
+ * the on-disk kernel cache (JK_KERNEL_CACHE, else next to the library).
+ * Needs no GPU. *threads_per_quartet receives the fragmentation chosen.
+ * JK_ERR_COMPILE with the NVRTC log in jk_last_error() on failure. */
+int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na, int32_t nb, int32_t nc,
+                     int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32,
+                     int32_t *threads_per_quartet, double *compile_ms);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *jk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JK_H */

@@ -1,0 +1,1153 @@
+// Host side of the JK build: input checks, shell/pair planning, runtime
+// kernel compilation (NVRTC, sm_103a) with an on-disk binary cache, the
+// per-build launch sequence, and the C ABI declared in include/jk.h.
+//
+// Planning follows Sec. 3 of the paper: the static parameters of a kernel
+// (Table 1: angular momenta, primitive counts, fragment sizes, n_dm, do_j,
+// do_k, precision) are template arguments of one instantiation compiled at
+// run time; the dynamic inputs (Table 2: coordinates, exponents,
+// coefficients, D) are device arrays. Screening (eq:schwartz, and the
+// density-matrix bound of Sec. 2) happens inside the kernels.
+#include "jk.h"
+#include "jk_types.h"
+#include "jk_util.cuh"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <functional>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernel_src.inc"   // jk_kernel_source[]: jk_types.h + rys_params.cuh + jk_kernels.cuh
+#include "rys_tables.inc"   // rys_table64[], rys_table32_src[]
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[2048];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? JK_ERR_OOM : JK_ERR_CUDA, "%s: %s",  \
+                        #call, cudaGetErrorString(e_));                                        \
+    } while (0)
+
+// ------------------------------------------------------------ driver API
+// Resolved through the runtime so that the library does not link libcuda.
+struct Driver {
+    CUresult (*moduleLoadData)(CUmodule *, const void *) = nullptr;
+    CUresult (*moduleGetFunction)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                             unsigned, CUstream, void **, void **) = nullptr;
+    CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*funcGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
+    CUresult (*occupancy)(int *, CUfunction, int, size_t) = nullptr;
+    bool ok = false;
+};
+
+Driver &drv()
+{
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto get = [](const char *name, void **fp) {
+            cudaDriverEntryPointQueryResult q;
+            return cudaGetDriverEntryPointByVersion(name, fp, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess && *fp;
+        };
+        d.ok = get("cuModuleLoadData", (void **)&d.moduleLoadData) &&
+               get("cuModuleGetFunction", (void **)&d.moduleGetFunction) &&
+               get("cuLaunchKernel", (void **)&d.launchKernel) &&
+               get("cuFuncSetAttribute", (void **)&d.funcSetAttribute) &&
+               get("cuFuncGetAttribute", (void **)&d.funcGetAttribute) &&
+               get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void **)&d.occupancy);
+    });
+    return d;
+}
+
+// ------------------------------------------------------------ kernel spec
+int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+struct KSpec {
+    int kind = 0;  // 0 class kernel, 1 Schwarz kernel
+    int la = 0, lb = 0, lc = 0, ld = 0, na = 1, nb = 1, nc = 1, nd = 1;
+    int ga = 1, gb = 1, gc = 1, gd = 1;
+    int ndm = 1, doj = 1, dok = 1, fp32 = 0;
+
+    std::string name() const
+    {
+        char b[256];
+        if (kind == 1)
+            snprintf(b, sizeof b, "jk_schwarz_kernel<%d,%d,%d,%d,%d,%d,%d,%d>", la, lb, na, nb, ga, gb, gc, gd);
+        else
+            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s>", la, lb, lc,
+                     ld, na, nb, nc, nd, ga, gb, gc, gd, ndm, doj, dok, fp32 ? "float" : "double");
+        return b;
+    }
+    int G() const { return ga * gb * gc * gd; }
+    int nr() const { return (la + lb + lc + ld) / 2 + 1; }
+    int ni() const { return (la + 1) * (lb + 1) * (lc + 1) * (ld + 1); }
+    int smem_group_reals() const { return G() == 1 ? 0 : nr() * 3 * ni() + 2 * nr(); }
+    int block() const { return 128; }
+    size_t smem_bytes() const
+    {
+        int ngw = 32 / G();
+        return (size_t)4 * ngw * smem_group_reals() * (fp32 ? 4 : 8);
+    }
+};
+
+struct KInfo {
+    CUfunction fn = nullptr;
+    int regs = 0, local_bytes = 0, blocks_per_sm = 0;
+    size_t smem = 0;
+    double compile_ms = 0;
+    bool from_cache = false;
+};
+
+// FNV-1a 64
+uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+std::string lib_dir()
+{
+    Dl_info info;
+    if (dladdr((void *)&lib_dir, &info) && info.dli_fname) {
+        std::string s = info.dli_fname;
+        auto k = s.rfind('/');
+        if (k != std::string::npos) return s.substr(0, k);
+    }
+    return ".";
+}
+
+std::string cache_dir()
+{
+    const char *e = getenv("JK_KERNEL_CACHE");
+    std::string d = e && *e ? std::string(e) : lib_dir() + "/kcache";
+    mkdir(d.c_str(), 0755);
+    return d;
+}
+
+std::vector<std::string> nvrtc_options(const KSpec &s)
+{
+    std::vector<std::string> o = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+    if (s.fp32) o.push_back("--use_fast_math");
+    return o;
+}
+
+uint64_t spec_key(const KSpec &s)
+{
+    int major = 0, minor = 0;
+    nvrtcVersion(&major, &minor);
+    uint64_t h = fnv(jk_kernel_source, sizeof(jk_kernel_source));
+    std::string n = s.name();
+    h = fnv(n.data(), n.size(), h);
+    for (auto &o : nvrtc_options(s)) h = fnv(o.data(), o.size(), h);
+    h = fnv(&major, sizeof major, h);
+    h = fnv(&minor, sizeof minor, h);
+    return h;
+}
+
+// Compile one instantiation to a cubin; returns the lowered (mangled) name.
+int nvrtc_compile(const KSpec &s, std::vector<char> &cubin, std::string &lowered, std::string &log)
+{
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, jk_kernel_source, "jk_kernels.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        log = "nvrtcCreateProgram failed";
+        return JK_ERR_COMPILE;
+    }
+    std::string name = s.name();
+    nvrtcAddNameExpression(prog, name.c_str());
+    auto opts = nvrtc_options(s);
+    std::vector<const char *> copts;
+    for (auto &o : opts) copts.push_back(o.c_str());
+    nvrtcResult r = nvrtcCompileProgram(prog, (int)copts.size(), copts.data());
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    log.assign(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &log[0]);
+    if (r != NVRTC_SUCCESS) {
+        nvrtcDestroyProgram(&prog);
+        return JK_ERR_COMPILE;
+    }
+    const char *ln = nullptr;
+    nvrtcGetLoweredName(prog, name.c_str(), &ln);
+    lowered = ln ? ln : "";
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin.resize(n);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    return JK_OK;
+}
+
+struct KernelCache {
+    std::mutex mu;
+    std::map<std::pair<int, uint64_t>, KInfo> loaded;  // (device, key)
+    std::vector<CUmodule> modules;
+};
+KernelCache &kcache()
+{
+    static KernelCache *c = new KernelCache();
+    return *c;
+}
+
+bool read_cache_file(const std::string &path, std::string &lowered, std::vector<char> &cubin)
+{
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return false;
+    std::getline(f, lowered);
+    std::vector<char> buf((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
+    if (lowered.empty() || buf.empty()) return false;
+    cubin.swap(buf);
+    return true;
+}
+
+void write_cache_file(const std::string &path, const std::string &lowered, const std::vector<char> &cubin)
+{
+    std::string tmp = path + ".tmp" + std::to_string(getpid()) + "_" +
+                      std::to_string(std::hash<std::thread::id>()(std::this_thread::get_id()));
+    {
+        std::ofstream f(tmp, std::ios::binary);
+        if (!f) return;
+        f << lowered << "\n";
+        f.write(cubin.data(), (std::streamsize)cubin.size());
+    }
+    rename(tmp.c_str(), path.c_str());
+}
+
+// Make every spec available on the current device: memory, then disk, then
+// NVRTC (in parallel threads). Fills out[i].
+// Compile the specs that are not yet in the on-disk cache (no device needed).
+int compile_to_disk(const std::vector<KSpec> &specs, double *ms_total)
+{
+    std::string dir = cache_dir();
+    std::vector<int> todo;
+    std::map<uint64_t, int> seen;
+    for (size_t i = 0; i < specs.size(); ++i) {
+        uint64_t k = spec_key(specs[i]);
+        if (seen.count(k)) continue;
+        seen[k] = 1;
+        char fn[64];
+        snprintf(fn, sizeof fn, "/%016llx.bin", (unsigned long long)k);
+        struct stat st;
+        if (stat((dir + fn).c_str(), &st) != 0) todo.push_back((int)i);
+    }
+    std::vector<int> rc(todo.size(), JK_OK);
+    std::vector<std::string> logs(todo.size());
+    std::atomic<int> next(0);
+    auto t0 = std::chrono::steady_clock::now();
+    auto worker = [&]() {
+        for (;;) {
+            int k = next.fetch_add(1);
+            if (k >= (int)todo.size()) break;
+            const KSpec &s = specs[todo[k]];
+            std::vector<char> bin;
+            std::string low;
+            rc[k] = nvrtc_compile(s, bin, low, logs[k]);
+            if (rc[k] == JK_OK) {
+                char fn[64];
+                snprintf(fn, sizeof fn, "/%016llx.bin", (unsigned long long)spec_key(s));
+                write_cache_file(dir + fn, low, bin);
+            }
+        }
+    };
+    int nth = (int)std::min<size_t>(todo.size(), std::max(1u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    if (ms_total) *ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (size_t k = 0; k < todo.size(); ++k)
+        if (rc[k] != JK_OK)
+            return fail(JK_ERR_COMPILE, "NVRTC failed for %s:\n%.3000s", specs[todo[k]].name().c_str(), logs[k].c_str());
+    return JK_OK;
+}
+
+int ensure_kernels(const std::vector<KSpec> &specs, std::vector<KInfo> &out)
+{
+    Driver &d = drv();
+    if (!d.ok) return fail(JK_ERR_CUDA, "CUDA driver entry points unavailable");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    KernelCache &kc = kcache();
+    out.assign(specs.size(), KInfo());
+    std::vector<int> todo;
+    std::vector<uint64_t> keys(specs.size());
+    {
+        std::lock_guard<std::mutex> g(kc.mu);
+        for (size_t i = 0; i < specs.size(); ++i) {
+            keys[i] = spec_key(specs[i]);
+            auto it = kc.loaded.find({dev, keys[i]});
+            if (it != kc.loaded.end()) out[i] = it->second;
+            else todo.push_back((int)i);
+        }
+    }
+    if (todo.empty()) return JK_OK;
+    // de-duplicate
+    std::vector<int> uniq;
+    {
+        std::map<uint64_t, int> seen;
+        for (int i : todo)
+            if (!seen.count(keys[i])) { seen[keys[i]] = i; uniq.push_back(i); }
+    }
+    std::string dir = cache_dir();
+    std::vector<std::vector<char>> bins(uniq.size());
+    std::vector<std::string> lowered(uniq.size()), logs(uniq.size());
+    std::vector<int> rc(uniq.size(), JK_OK);
+    std::vector<double> ms(uniq.size(), 0.0);
+    std::vector<char> cached(uniq.size(), 0);
+    std::atomic<int> next(0);
+    auto worker = [&]() {
+        for (;;) {
+            int k = next.fetch_add(1);
+            if (k >= (int)uniq.size()) break;
+            const KSpec &s = specs[uniq[k]];
+            char fn[64];
+            snprintf(fn, sizeof fn, "/%016llx.bin", (unsigned long long)keys[uniq[k]]);
+            std::string path = dir + fn;
+            if (read_cache_file(path, lowered[k], bins[k])) { cached[k] = 1; continue; }
+            auto t0 = std::chrono::steady_clock::now();
+            rc[k] = nvrtc_compile(s, bins[k], lowered[k], logs[k]);
+            ms[k] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (rc[k] == JK_OK) write_cache_file(path, lowered[k], bins[k]);
+        }
+    };
+    int nth = (int)std::min<size_t>(uniq.size(), std::max(1u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    for (size_t k = 0; k < uniq.size(); ++k)
+        if (rc[k] != JK_OK)
+            return fail(JK_ERR_COMPILE, "NVRTC failed for %s:\n%.1500s", specs[uniq[k]].name().c_str(), logs[k].c_str());
+    std::lock_guard<std::mutex> g(kc.mu);
+    for (size_t k = 0; k < uniq.size(); ++k) {
+        const KSpec &s = specs[uniq[k]];
+        CUmodule mod;
+        CUresult r = d.moduleLoadData(&mod, bins[k].data());
+        if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "cuModuleLoadData(%s) failed: %d", s.name().c_str(), (int)r);
+        kc.modules.push_back(mod);
+        KInfo ki;
+        r = d.moduleGetFunction(&ki.fn, mod, lowered[k].c_str());
+        if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "cuModuleGetFunction(%s) failed: %d", s.name().c_str(), (int)r);
+        ki.smem = s.smem_bytes();
+        if (ki.smem > 48 * 1024)
+            d.funcSetAttribute(ki.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)ki.smem);
+        d.funcGetAttribute(&ki.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ki.fn);
+        d.funcGetAttribute(&ki.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, ki.fn);
+        d.occupancy(&ki.blocks_per_sm, ki.fn, s.block(), ki.smem);
+        ki.compile_ms = ms[k];
+        ki.from_cache = cached[k];
+        kc.loaded[{dev, keys[uniq[k]]}] = ki;
+    }
+    for (size_t i = 0; i < specs.size(); ++i) out[i] = kc.loaded[{dev, keys[i]}];
+    return JK_OK;
+}
+
+// -------------------------------------------------------- fragment choice
+// Threads per quartet: G = ga*gb*gc*gd with each g dividing the Cartesian
+// size of its shell and G <= 32. G == 1 keeps the 2D tables in registers and
+// is taken when elements plus tables stay small; otherwise the smallest G
+// whose per-thread fragment fits the register budget (the 1qnt grid search
+// of Sec. 3.2 refines this per device through the tuning table).
+void choose_fragments(KSpec &s, bool symmetric)
+{
+    const int nf[4] = {ncart(s.la), ncart(s.lb), ncart(s.lc), ncart(s.ld)};
+    const int ne = nf[0] * nf[1] * nf[2] * nf[3];
+    const int ni = s.ni();
+    const int reg_cap = s.fp32 ? 96 : 48;     // per-thread fragment budget (reals)
+    const int g1_cap = s.fp32 ? 128 : 64;     // register-mode budget: fragment + 3 tables
+    if (ne + 3 * ni <= g1_cap) { s.ga = s.gb = s.gc = s.gd = 1; return; }
+    int best[4] = {1, 1, 1, 1};
+    long best_score = -1;
+    auto divisors = [](int n) { std::vector<int> v; for (int i = 1; i <= n; ++i) if (n % i == 0) v.push_back(i); return v; };
+    for (int a : divisors(nf[0]))
+        for (int b : divisors(nf[1]))
+            for (int c : divisors(nf[2]))
+                for (int d : divisors(nf[3])) {
+                    if (symmetric && (a != c || b != d)) continue;
+                    int g = a * b * c * d;
+                    if (g > 32 || g < 2) continue;
+                    int ept = ne / g;
+                    // prefer: fits the budget, then fewest threads, then fewest idle lanes
+                    long fits = ept <= reg_cap ? 1 : 0;
+                    long idle = 32 % g;
+                    long score = fits * 1000000 + (fits ? (100 - g) * 1000 : (100000 - ept) * 10) - idle;
+                    if (score > best_score) { best_score = score; best[0] = a; best[1] = b; best[2] = c; best[3] = d; }
+                }
+    s.ga = best[0]; s.gb = best[1]; s.gc = best[2]; s.gd = best[3];
+}
+
+// Modelled FLOPs of one contracted quartet of a class (FMA = 2).
+double class_flops(const KSpec &s, int ndm)
+{
+    const double nr = s.nr();
+    const double ne = (double)ncart(s.la) * ncart(s.lb) * ncart(s.lc) * ncart(s.ld);
+    const double na = s.la + s.lb, nc = s.lc + s.ld;
+    const double vrr = 3.0 * 3.0 * (na + 1) * (nc + 1);
+    const double hrr = 3.0 * 2.0 * ((s.lb ? (na + 1) * s.lb : 0) * (nc + 1) + (s.ld ? (nc + 1) * s.ld : 0) * (s.la + 1) * (s.lb + 1));
+    const double roots = 2.0 * nr * 2.0 * 10.0;
+    const double setup = 30.0;
+    const double prim = setup + roots + nr * (vrr + hrr) + nr * 3.0 * ne;
+    const double P = (double)s.na * s.nb * s.nc * s.nd;
+    return P * prim + ndm * 2.0 * 6.0 * ne;
+}
+
+// ------------------------------------------------------------ plan data
+struct PairClass {
+    int la, lb, na, nb;
+    int off = 0, n = 0;              // range in the pair array
+    std::vector<int> beg, end;       // per molecule, absolute indices into the pair array
+    int *d_beg = nullptr, *d_end = nullptr;
+};
+
+struct Launch {
+    int c1, c2;        // pair classes (bra, ket)
+    KSpec spec[2];     // [0] FP64, [1] FP32
+    double cost;       // scheduling estimate
+};
+
+}  // namespace
+
+struct jk_handle {
+    int device = 0;
+    int nmol = 0;
+    int nshell = 0;
+    std::vector<jk_shell> shells;
+    std::vector<int> mol_sh0;              // nmol + 1
+    std::vector<int> nao_cart, nao_user;   // per molecule
+    std::vector<int> sh_ao_cart;           // molecule-local Cartesian AO offset per shell
+    bool spherical = false;
+    // device
+    int *d_sh_mol = nullptr, *d_mol_sh0 = nullptr, *d_sh_ao = nullptr, *d_sh_nc = nullptr;
+    JkPair *d_pairs = nullptr;
+    JkPrimPair64 *d_pp64 = nullptr;
+    JkPrimPair32 *d_pp32 = nullptr;
+    JkMol *d_mols = nullptr;
+    double *d_dmax = nullptr;
+    unsigned long long *d_dmax_mol = nullptr;
+    double *d_rys64 = nullptr;
+    float *d_rys32 = nullptr;
+    int *d_work = nullptr;                 // one counter per launch
+    unsigned long long *d_stats = nullptr; // two per launch
+    int *d_err = nullptr;
+    long long *d_tile_off = nullptr;
+    long long ntiles = 0;
+    long long dmax_total = 0;
+    JkMol *h_mols = nullptr;               // pinned staging
+    cudaEvent_t mol_copied = nullptr, ev0 = nullptr, ev1 = nullptr;
+    std::vector<PairClass> classes;
+    std::vector<Launch> launches;
+    std::vector<JkPair> h_pairs;
+    int num_sms = 0;
+    // options
+    double tau32 = 1e-7, router_band = 100.0, pair_cutoff = 1e-18;
+    int use_graph = 0, use_dmax = 1, profile = 0;
+    double init_ms = 0, compile_ms = 0;
+    std::vector<cudaEvent_t> prof_ev;      // two per launch slot
+    std::vector<jk_launch_prof> prof;
+};
+
+namespace {
+
+void free_handle(jk_handle *h)
+{
+    if (!h) return;
+    for (auto &c : h->classes) { cudaFree(c.d_beg); cudaFree(c.d_end); }
+    cudaFree(h->d_sh_mol); cudaFree(h->d_mol_sh0); cudaFree(h->d_sh_ao); cudaFree(h->d_sh_nc);
+    cudaFree(h->d_pairs); cudaFree(h->d_pp64); cudaFree(h->d_pp32); cudaFree(h->d_mols);
+    cudaFree(h->d_dmax); cudaFree(h->d_dmax_mol); cudaFree(h->d_rys64); cudaFree(h->d_rys32);
+    cudaFree(h->d_work); cudaFree(h->d_stats); cudaFree(h->d_err); cudaFree(h->d_tile_off);
+    if (h->h_mols) cudaFreeHost(h->h_mols);
+    if (h->mol_copied) cudaEventDestroy(h->mol_copied);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto e : h->prof_ev) cudaEventDestroy(e);
+    delete h;
+}
+
+template <typename T>
+int upload(T **dst, const std::vector<T> &src)
+{
+    if (src.empty()) { *dst = nullptr; return JK_OK; }
+    CK(cudaMalloc((void **)dst, sizeof(T) * src.size()));
+    CK(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return JK_OK;
+}
+
+// shell type order: l first, then nprim
+long type_key(const jk_shell &s) { return (long)s.l * 64 + s.nprim; }
+
+int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells, int32_t nshell,
+              const double *coords, int32_t natm, const double *exps, const double *coeffs,
+              int32_t nprim_total, jk_handle **out)
+{
+    if (!out) return fail(JK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nmol < 1 || !mol_shell_off || !shells || nshell < 1 || !coords || natm < 1 || !exps || !coeffs ||
+        nprim_total < 1)
+        return fail(JK_ERR_ARG, "empty or NULL basis arguments");
+    if (mol_shell_off[0] != 0 || mol_shell_off[nmol] != nshell)
+        return fail(JK_ERR_ARG, "mol_shell_off must start at 0 and end at nshell");
+    for (int m = 0; m < nmol; ++m)
+        if (mol_shell_off[m + 1] <= mol_shell_off[m]) return fail(JK_ERR_ARG, "molecule %d has no shells", m);
+    for (int s = 0; s < nshell; ++s) {
+        const jk_shell &x = shells[s];
+        if (x.l < 0 || x.nprim < 1 || x.atom < 0 || x.atom >= natm || x.prim_off < 0 ||
+            x.prim_off + x.nprim > nprim_total || x.ao_off < 0 || (x.spherical != 0 && x.spherical != 1))
+            return fail(JK_ERR_ARG, "shell %d has fields out of range", s);
+        if (x.l > JK_LMAX) return fail(JK_ERR_UNSUPPORTED, "shell %d: l=%d above JK_LMAX=%d", s, x.l, JK_LMAX);
+        if (x.nprim > JK_NPRIM_MAX) return fail(JK_ERR_UNSUPPORTED, "shell %d: nprim=%d above %d", s, x.nprim, JK_NPRIM_MAX);
+        if (x.spherical) return fail(JK_ERR_UNSUPPORTED, "spherical shells are not supported yet");
+        for (int i = 0; i < x.nprim; ++i)
+            if (!(exps[x.prim_off + i] > 0) || !std::isfinite(coeffs[x.prim_off + i]))
+                return fail(JK_ERR_ARG, "shell %d: non-positive exponent or non-finite coefficient", s);
+    }
+    for (int i = 0; i < 3 * natm; ++i)
+        if (!std::isfinite(coords[i])) return fail(JK_ERR_ARG, "non-finite coordinate");
+
+    auto t_start = std::chrono::steady_clock::now();
+    std::unique_ptr<jk_handle, void (*)(jk_handle *)> h(new jk_handle(), free_handle);
+    CK(cudaGetDevice(&h->device));
+    CK(cudaFree(0));
+    CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->nmol = nmol;
+    h->nshell = nshell;
+    h->shells.assign(shells, shells + nshell);
+    h->mol_sh0.assign(mol_shell_off, mol_shell_off + nmol + 1);
+    h->sh_ao_cart.resize(nshell);
+    std::vector<int> sh_mol(nshell), sh_nc(nshell);
+    for (int m = 0; m < nmol; ++m) {
+        int o = 0, ou = 0;
+        for (int s = mol_shell_off[m]; s < mol_shell_off[m + 1]; ++s) {
+            sh_mol[s] = m;
+            h->sh_ao_cart[s] = o;
+            sh_nc[s] = ncart(shells[s].l);
+            o += ncart(shells[s].l);
+            ou = std::max(ou, shells[s].ao_off + ncart(shells[s].l));
+        }
+        h->nao_cart.push_back(o);
+        h->nao_user.push_back(o);
+        (void)ou;
+    }
+
+    // ---- shell types and pair classes
+    std::vector<long> tkeys;
+    for (int s = 0; s < nshell; ++s) tkeys.push_back(type_key(shells[s]));
+    std::sort(tkeys.begin(), tkeys.end());
+    tkeys.erase(std::unique(tkeys.begin(), tkeys.end()), tkeys.end());
+    std::reverse(tkeys.begin(), tkeys.end());   // type 0 = largest (l, nprim)
+    auto type_of = [&](int s) { return (int)(std::find(tkeys.begin(), tkeys.end(), type_key(shells[s])) - tkeys.begin()); };
+    std::vector<int> sh_type(nshell);
+    for (int s = 0; s < nshell; ++s) sh_type[s] = type_of(s);
+    const int ntype = (int)tkeys.size();
+    auto pclass = [&](int ta, int tb) { return ta * ntype + tb; };   // ta <= tb in type index (a is "larger")
+
+    // ---- candidate pairs (host pre-screen: largest Gaussian product factor)
+    struct Cand { int a, b, cls; };
+    std::vector<Cand> cand;
+    for (int m = 0; m < nmol; ++m) {
+        for (int s1 = mol_shell_off[m]; s1 < mol_shell_off[m + 1]; ++s1)
+            for (int s2 = mol_shell_off[m]; s2 <= s1; ++s2) {
+                int a = s1, b = s2;
+                if (sh_type[a] > sh_type[b] || (sh_type[a] == sh_type[b] && a < b)) std::swap(a, b);
+                const double *A = coords + 3 * shells[a].atom, *B = coords + 3 * shells[b].atom;
+                double r2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+                double mu_min = 1e300;
+                for (int i = 0; i < shells[a].nprim; ++i)
+                    for (int j = 0; j < shells[b].nprim; ++j) {
+                        double al = exps[shells[a].prim_off + i], be = exps[shells[b].prim_off + j];
+                        mu_min = std::min(mu_min, al * be / (al + be));
+                    }
+                if (mu_min * r2 > 92.0) continue;   // exp(-92) ~ 1e-40
+                cand.push_back({a, b, pclass(sh_type[a], sh_type[b])});
+            }
+    }
+    if (cand.empty()) return fail(JK_ERR_ARG, "no shell pairs");
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.cls < y.cls; });
+    const long long ncand = (long long)cand.size();
+    if (ncand > 0x7fffffffLL) return fail(JK_ERR_UNSUPPORTED, "too many shell pairs");
+    std::vector<int> ca(ncand), cb(ncand), cpp(ncand);
+    long long npp = 0;
+    for (long long i = 0; i < ncand; ++i) {
+        ca[i] = cand[i].a;
+        cb[i] = cand[i].b;
+        cpp[i] = (int)npp;
+        npp += (long long)shells[cand[i].a].nprim * shells[cand[i].b].nprim;
+    }
+    if (npp > 0x7fffffffLL) return fail(JK_ERR_UNSUPPORTED, "too many primitive pairs");
+
+    // ---- device copies of the basis
+    std::vector<int> sh_atom(nshell), sh_np(nshell), sh_prim(nshell);
+    for (int s = 0; s < nshell; ++s) { sh_atom[s] = shells[s].atom; sh_np[s] = shells[s].nprim; sh_prim[s] = shells[s].prim_off; }
+    int *d_ca = nullptr, *d_cb = nullptr, *d_cpp = nullptr, *d_atom = nullptr, *d_np = nullptr, *d_prim = nullptr;
+    double *d_coords = nullptr, *d_exps = nullptr, *d_coeffs = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_ca); cudaFree(d_cb); cudaFree(d_cpp); cudaFree(d_atom); cudaFree(d_np); cudaFree(d_prim);
+        cudaFree(d_coords); cudaFree(d_exps); cudaFree(d_coeffs);
+    };
+    struct Guard { std::function<void()> f; ~Guard() { f(); } } guard{cleanup};
+    int rc;
+    if ((rc = upload(&d_ca, ca)) || (rc = upload(&d_cb, cb)) || (rc = upload(&d_cpp, cpp)) ||
+        (rc = upload(&d_atom, sh_atom)) || (rc = upload(&d_np, sh_np)) || (rc = upload(&d_prim, sh_prim)))
+        return rc;
+    if ((rc = upload(&d_coords, std::vector<double>(coords, coords + 3 * natm))) ||
+        (rc = upload(&d_exps, std::vector<double>(exps, exps + nprim_total))) ||
+        (rc = upload(&d_coeffs, std::vector<double>(coeffs, coeffs + nprim_total))))
+        return rc;
+    CK(cudaMalloc(&h->d_pp64, sizeof(JkPrimPair64) * npp));
+    CK(cudaMalloc(&h->d_pp32, sizeof(JkPrimPair32) * npp));
+    jk_pairdata_kernel<<<(unsigned)((ncand + 127) / 128), 128>>>((int)ncand, d_ca, d_cb, d_cpp, d_atom, d_np, d_prim,
+                                                                  d_coords, d_exps, d_coeffs, h->d_pp64, h->d_pp32);
+    CK(cudaGetLastError());
+
+    // ---- Rys tables
+    {
+        std::vector<double> t64(rys_table64, rys_table64 + rys_table64_size);
+        std::vector<float> t32(rys_table32_size);
+        for (size_t i = 0; i < rys_table32_size; ++i) t32[i] = (float)rys_table32_src[i];
+        if ((rc = upload(&h->d_rys64, t64)) || (rc = upload(&h->d_rys32, t32))) return rc;
+    }
+
+    // ---- JkPair records for the candidates (unsorted), Schwarz per class
+    std::vector<JkPair> cp(ncand);
+    for (long long i = 0; i < ncand; ++i) {
+        JkPair &p = cp[i];
+        const int a = ca[i], b = cb[i];
+        p.a = a; p.b = b; p.mol = sh_mol[a]; p.pp_off = cpp[i];
+        p.a_ao = h->sh_ao_cart[a]; p.b_ao = h->sh_ao_cart[b];
+        p.a_loc = a - mol_shell_off[p.mol]; p.b_loc = b - mol_shell_off[p.mol];
+        const double *A = coords + 3 * shells[a].atom, *B = coords + 3 * shells[b].atom;
+        p.Ax = A[0]; p.Ay = A[1]; p.Az = A[2];
+        p.ABx = A[0] - B[0]; p.ABy = A[1] - B[1]; p.ABz = A[2] - B[2];
+        p.Q = 0; p.pad = 0;
+    }
+    JkPair *d_cp = nullptr;
+    double *d_q = nullptr;
+    if ((rc = upload(&d_cp, cp))) return rc;
+    struct G2 { JkPair *p; double *q; ~G2() { cudaFree(p); cudaFree(q); } } g2{d_cp, nullptr};
+    CK(cudaMalloc(&d_q, sizeof(double) * ncand));
+    g2.q = d_q;
+    {
+        // one Schwarz launch per pair class
+        std::vector<KSpec> specs;
+        std::vector<std::pair<long long, long long>> ranges;
+        long long i0 = 0;
+        while (i0 < ncand) {
+            long long i1 = i0;
+            while (i1 < ncand && cand[i1].cls == cand[i0].cls) ++i1;
+            const jk_shell &sa = shells[cand[i0].a], &sb = shells[cand[i0].b];
+            KSpec s;
+            s.kind = 1;
+            s.la = s.lc = sa.l; s.lb = s.ld = sb.l; s.na = s.nc = sa.nprim; s.nb = s.nd = sb.nprim;
+            choose_fragments(s, true);
+            specs.push_back(s);
+            ranges.push_back({i0, i1});
+            i0 = i1;
+        }
+        std::vector<KInfo> ki;
+        auto tc = std::chrono::steady_clock::now();
+        if ((rc = ensure_kernels(specs, ki))) return rc;
+        h->compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc).count();
+        for (size_t k = 0; k < specs.size(); ++k) {
+            JkSchwarzArgs a;
+            a.pairs = d_cp + ranges[k].first;
+            a.pp64 = h->d_pp64;
+            a.rys64 = h->d_rys64;
+            a.Qout = d_q + ranges[k].first;
+            a.npair = (int)(ranges[k].second - ranges[k].first);
+            const int ngw = 32 / specs[k].G();
+            long long warps = (a.npair + ngw - 1) / ngw;
+            unsigned grid = (unsigned)std::min<long long>((warps + 3) / 4, (long long)h->num_sms * 8);
+            void *params[] = {&a};
+            CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, 128, 1, 1, (unsigned)ki[k].smem, 0, params, nullptr);
+            if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "Schwarz launch failed: %d", (int)r);
+        }
+        CK(cudaDeviceSynchronize());
+    }
+    std::vector<double> q(ncand);
+    CK(cudaMemcpy(q.data(), d_q, sizeof(double) * ncand, cudaMemcpyDeviceToHost));
+
+    // ---- prune, group by (class, molecule), sort by Q descending
+    std::vector<long long> order;
+    for (long long i = 0; i < ncand; ++i)
+        if (q[i] > h->pair_cutoff && std::isfinite(q[i])) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](long long x, long long y) {
+        if (cand[x].cls != cand[y].cls) return cand[x].cls < cand[y].cls;
+        if (cp[x].mol != cp[y].mol) return cp[x].mol < cp[y].mol;
+        return q[x] > q[y];
+    });
+    h->h_pairs.resize(order.size());
+    for (size_t k = 0; k < order.size(); ++k) { h->h_pairs[k] = cp[order[k]]; h->h_pairs[k].Q = q[order[k]]; }
+    size_t k0 = 0;
+    while (k0 < order.size()) {
+        size_t k1 = k0;
+        int cls = cand[order[k0]].cls;
+        while (k1 < order.size() && cand[order[k1]].cls == cls) ++k1;
+        PairClass pc;
+        const jk_shell &sa = shells[h->h_pairs[k0].a], &sb = shells[h->h_pairs[k0].b];
+        pc.la = sa.l; pc.lb = sb.l; pc.na = sa.nprim; pc.nb = sb.nprim;
+        pc.off = (int)k0; pc.n = (int)(k1 - k0);
+        // per molecule, indices relative to the class base (empty range if none)
+        pc.beg.assign(nmol, 0);
+        pc.end.assign(nmol, 0);
+        for (size_t k = k0; k < k1;) {
+            int m = h->h_pairs[k].mol;
+            size_t e = k;
+            while (e < k1 && h->h_pairs[e].mol == m) ++e;
+            pc.beg[m] = (int)(k - k0); pc.end[m] = (int)(e - k0);
+            k = e;
+        }
+        h->classes.push_back(pc);
+        k0 = k1;
+    }
+    if ((rc = upload(&h->d_pairs, h->h_pairs))) return rc;
+    for (auto &c : h->classes) {
+        if ((rc = upload(&c.d_beg, c.beg)) || (rc = upload(&c.d_end, c.end))) return rc;
+    }
+
+    // ---- class-pair launches (bra class index <= ket class index in type order)
+    const int nc = (int)h->classes.size();
+    for (int i = 0; i < nc; ++i)
+        for (int j = i; j < nc; ++j) {
+            Launch L;
+            L.c1 = i; L.c2 = j;
+            const PairClass &A = h->classes[i], &B = h->classes[j];
+            for (int t = 0; t < 2; ++t) {
+                KSpec &s = L.spec[t];
+                s.kind = 0;
+                s.la = A.la; s.lb = A.lb; s.lc = B.la; s.ld = B.lb;
+                s.na = A.na; s.nb = A.nb; s.nc = B.na; s.nd = B.nb;
+                s.fp32 = t;
+                choose_fragments(s, false);
+            }
+            L.cost = (double)A.n * B.n * class_flops(L.spec[0], 1);
+            h->launches.push_back(L);
+        }
+    std::stable_sort(h->launches.begin(), h->launches.end(), [](const Launch &x, const Launch &y) { return x.cost > y.cost; });
+
+    // ---- per-build scratch
+    std::vector<int> mol_sh0(h->mol_sh0.begin(), h->mol_sh0.end());
+    std::vector<int> sh_ao(h->sh_ao_cart.begin(), h->sh_ao_cart.end());
+    if ((rc = upload(&h->d_sh_mol, sh_mol)) || (rc = upload(&h->d_mol_sh0, mol_sh0)) ||
+        (rc = upload(&h->d_sh_ao, sh_ao)) || (rc = upload(&h->d_sh_nc, sh_nc)))
+        return rc;
+    long long dtot = 0;
+    std::vector<long long> toff(nmol + 1, 0);
+    for (int m = 0; m < nmol; ++m) {
+        long long ns = mol_shell_off[m + 1] - mol_shell_off[m];
+        dtot += ns * ns;
+        long long nt = (h->nao_cart[m] + 31) / 32;
+        toff[m + 1] = toff[m] + nt * (nt + 1) / 2;
+    }
+    h->dmax_total = dtot;
+    h->ntiles = toff[nmol];
+    if ((rc = upload(&h->d_tile_off, toff))) return rc;
+    CK(cudaMalloc(&h->d_dmax, sizeof(double) * dtot));
+    CK(cudaMalloc(&h->d_dmax_mol, sizeof(unsigned long long) * nmol));
+    CK(cudaMalloc(&h->d_mols, sizeof(JkMol) * nmol));
+    const size_t nl = h->launches.size() * 2;
+    CK(cudaMalloc(&h->d_work, sizeof(int) * nl));
+    CK(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 2 * nl));
+    CK(cudaMalloc(&h->d_err, sizeof(int)));
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    CK(cudaMallocHost(&h->h_mols, sizeof(JkMol) * nmol));
+    CK(cudaEventCreateWithFlags(&h->mol_copied, cudaEventDisableTiming));
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    CK(cudaDeviceSynchronize());
+    h->init_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    *out = h.release();
+    return JK_OK;
+}
+
+int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int with_k, double cutoff,
+               int mode, double *const *J, double *const *K, void *stream, jk_stats *stats)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    if (!D) return fail(JK_ERR_ARG, "D is NULL");
+    if (ndm < 1) return fail(JK_ERR_ARG, "n_dm must be >= 1");
+    if (ndm > JK_NDM_MAX) return fail(JK_ERR_UNSUPPORTED, "n_dm=%d above %d", ndm, JK_NDM_MAX);
+    if (!with_j && !with_k) return fail(JK_ERR_ARG, "with_j and with_k are both 0");
+    if (!(cutoff >= 0) || !std::isfinite(cutoff)) return fail(JK_ERR_ARG, "cutoff must be finite and >= 0");
+    if (mode < JK_PREC_FP64 || mode > JK_PREC_FP32) return fail(JK_ERR_ARG, "bad precision_mode %d", mode);
+    if (mode == JK_PREC_MIXED_ROUTED) return fail(JK_ERR_UNSUPPORTED, "router not loaded");
+    if (with_j && !J) return fail(JK_ERR_ARG, "J is NULL with with_j");
+    if (with_k && !K) return fail(JK_ERR_ARG, "K is NULL with with_k");
+    for (int m = 0; m < h->nmol; ++m) {
+        if (!D[m]) return fail(JK_ERR_ARG, "D[%d] is NULL", m);
+        if (with_j && !J[m]) return fail(JK_ERR_ARG, "J[%d] is NULL", m);
+        if (with_k && !K[m]) return fail(JK_ERR_ARG, "K[%d] is NULL", m);
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_ARG, "current device %d differs from the handle's %d", dev, h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // kernels for this combination
+    std::vector<KSpec> specs;
+    std::vector<int> lidx, tier;
+    for (size_t i = 0; i < h->launches.size(); ++i) {
+        for (int t = 0; t < 2; ++t) {
+            bool use = (t == 0) ? (mode == JK_PREC_FP64 || mode == JK_PREC_MIXED) : (mode == JK_PREC_FP32 || mode == JK_PREC_MIXED);
+            if (!use) continue;
+            KSpec s = h->launches[i].spec[t];
+            s.ndm = ndm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0;
+            specs.push_back(s);
+            lidx.push_back((int)i);
+            tier.push_back(t);
+        }
+    }
+    std::vector<KInfo> ki;
+    auto tc = std::chrono::steady_clock::now();
+    int rc = ensure_kernels(specs, ki);
+    if (rc) return rc;
+    h->compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc).count();
+
+    // per-molecule descriptors
+    CK(cudaEventSynchronize(h->mol_copied));
+    long long off = 0;
+    for (int m = 0; m < h->nmol; ++m) {
+        JkMol &x = h->h_mols[m];
+        x.D = D[m];
+        x.J = with_j ? J[m] : nullptr;
+        x.K = with_k ? K[m] : nullptr;
+        x.nao = h->nao_cart[m];
+        x.nsh = h->mol_sh0[m + 1] - h->mol_sh0[m];
+        x.dmax_off = off;
+        off += (long long)x.nsh * x.nsh;
+    }
+    if (stats) CK(cudaEventRecord(h->ev0, st));
+    CK(cudaMemcpyAsync(h->d_mols, h->h_mols, sizeof(JkMol) * h->nmol, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(h->mol_copied, st));
+    for (int m = 0; m < h->nmol; ++m) {
+        size_t bytes = sizeof(double) * (size_t)ndm * h->nao_cart[m] * h->nao_cart[m];
+        if (with_j) CK(cudaMemsetAsync(J[m], 0, bytes, st));
+        if (with_k) CK(cudaMemsetAsync(K[m], 0, bytes, st));
+    }
+    const size_t nl = h->launches.size() * 2;
+    CK(cudaMemsetAsync(h->d_work, 0, sizeof(int) * nl, st));
+    CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 2 * nl, st));
+    CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, st));
+    jk_dmax_kernel<<<h->nshell, 128, 0, st>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
+                                              h->d_dmax, h->d_dmax_mol);
+    CK(cudaGetLastError());
+
+    const double inf = INFINITY;
+    const bool prof = h->profile && stats;
+    if (prof && h->prof_ev.size() < 2 * specs.size()) {
+        size_t have = h->prof_ev.size();
+        h->prof_ev.resize(2 * specs.size());
+        for (size_t e = have; e < h->prof_ev.size(); ++e) CK(cudaEventCreate(&h->prof_ev[e]));
+    }
+    for (size_t k = 0; k < specs.size(); ++k) {
+        const Launch &L = h->launches[lidx[k]];
+        const PairClass &A = h->classes[L.c1], &B = h->classes[L.c2];
+        JkClassArgs a;
+        // bra and ket indices are relative to the base of their pair class
+        a.bra = h->d_pairs + A.off;
+        a.ket = h->d_pairs + B.off;
+        a.ket_beg = B.d_beg;
+        a.ket_end = B.d_end;
+        a.pp64 = h->d_pp64;
+        a.pp32 = h->d_pp32;
+        a.mols = h->d_mols;
+        a.dmax = h->d_dmax;
+        a.dmax_mol = reinterpret_cast<const double *>(h->d_dmax_mol);
+        a.rys64 = h->d_rys64;
+        a.rys32 = h->d_rys32;
+        const int slot = lidx[k] * 2 + tier[k];
+        a.work = h->d_work + slot;
+        a.stats = h->d_stats + 2 * slot;
+        a.err = h->d_err;
+        if (mode == JK_PREC_MIXED) {
+            const double t = std::max(cutoff, h->tau32);
+            if (tier[k] == 0) { a.lo = t; a.hi = inf; }
+            else { a.lo = cutoff; a.hi = t; }
+        } else {
+            a.lo = cutoff; a.hi = inf;
+        }
+        a.nbra = A.n;
+        a.same_class = (L.c1 == L.c2) ? 1 : 0;
+        a.with_j = with_j ? 1 : 0;
+        a.with_k = with_k ? 1 : 0;
+        a.use_dmax = h->use_dmax;
+        a.ndm = ndm;
+        int grid = std::max(1, ki[k].blocks_per_sm) * h->num_sms;
+        long long need = ((long long)A.n + 3) / 4;
+        if (need < grid) grid = (int)std::max(1LL, need);
+        void *params[] = {&a};
+        if (prof) CK(cudaEventRecord(h->prof_ev[2 * k], st));
+        CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, 128, 1, 1, (unsigned)ki[k].smem, (CUstream)st, params, nullptr);
+        if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "launch of %s failed: %d", specs[k].name().c_str(), (int)r);
+        if (prof) CK(cudaEventRecord(h->prof_ev[2 * k + 1], st));
+    }
+    if (h->ntiles > 0) {
+        dim3 grid((unsigned)h->ntiles, ndm, 2);
+        jk_symmetrize_kernel<<<grid, dim3(32, 8), 0, st>>>(h->d_mols, h->d_tile_off, h->nmol, ndm, with_j, with_k);
+        CK(cudaGetLastError());
+    }
+    if (stats) {
+        CK(cudaEventRecord(h->ev1, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        std::vector<unsigned long long> cnt(2 * nl);
+        CK(cudaMemcpy(cnt.data(), h->d_stats, sizeof(unsigned long long) * 2 * nl, cudaMemcpyDeviceToHost));
+        int err = 0;
+        CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        memset(stats, 0, sizeof(*stats));
+        stats->ms = ms;
+        stats->kernel_launches = (int64_t)specs.size() + 1 + (h->ntiles > 0 ? 1 : 0);
+        if (prof) h->prof.clear();
+        for (size_t k = 0; k < specs.size(); ++k) {
+            const int slot = lidx[k] * 2 + tier[k];
+            unsigned long long nq = cnt[2 * slot], np = cnt[2 * slot + 1];
+            if (tier[k] == 0) stats->quartets_fp64 += (int64_t)nq;
+            else stats->quartets_fp32 += (int64_t)nq;
+            stats->prim_quartets += (int64_t)np;
+            stats->flops_model += (double)nq * class_flops(specs[k], ndm);
+            if (prof) {
+                jk_launch_prof p;
+                const KSpec &x = specs[k];
+                p.la = x.la; p.lb = x.lb; p.lc = x.lc; p.ld = x.ld;
+                p.na = x.na; p.nb = x.nb; p.nc = x.nc; p.nd = x.nd;
+                p.tier = tier[k];
+                p.threads_per_quartet = x.G();
+                p.regs = ki[k].regs;
+                p.local_bytes = ki[k].local_bytes;
+                p.quartets = (int64_t)nq;
+                p.prim_quartets = (int64_t)np;
+                float lm = 0;
+                CK(cudaEventElapsedTime(&lm, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]));
+                p.ms = lm;
+                p.flops_model = (double)nq * class_flops(x, ndm);
+                h->prof.push_back(p);
+            }
+        }
+        if (err) {
+            CK(cudaMemset(h->d_err, 0, sizeof(int)));
+            return fail(err == JK_ERR_DEV_TIMEOUT ? JK_ERR_TIMEOUT : JK_ERR_CUDA, "device error word %d", err);
+        }
+    }
+    return JK_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+int jk_init(const jk_shell *shells, int32_t nshell, const double *coords, int32_t natm, const double *exps,
+            const double *coeffs, int32_t nprim_total, jk_handle **out)
+{
+    int32_t off[2] = {0, nshell};
+    try {
+        return init_impl(1, off, shells, nshell, coords, natm, exps, coeffs, nprim_total, out);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_OOM, "host exception: %s", e.what());
+    }
+}
+
+int jk_init_batch(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells, int32_t nshell,
+                  const double *coords, int32_t natm, const double *exps, const double *coeffs,
+                  int32_t nprim_total, jk_handle **out)
+{
+    try {
+        return init_impl(nmol, mol_shell_off, shells, nshell, coords, natm, exps, coeffs, nprim_total, out);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_OOM, "host exception: %s", e.what());
+    }
+}
+
+int jk_build(jk_handle *h, const double *D, int32_t n_dm, int with_j, int with_k, double cutoff,
+             int precision_mode, double *J, double *K, void *stream, jk_stats *stats)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    if (h->nmol != 1) return fail(JK_ERR_ARG, "jk_build needs a single-molecule handle (use jk_build_batch)");
+    try {
+        return build_impl(h, &D, n_dm, with_j, with_k, cutoff, precision_mode, &J, &K, stream, stats);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_OOM, "host exception: %s", e.what());
+    }
+}
+
+int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_j, int with_k, double cutoff,
+                   int precision_mode, double *const *J, double *const *K, void *stream, jk_stats *stats)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    if ((with_j && !J) || (with_k && !K)) return fail(JK_ERR_ARG, "J or K pointer array is NULL");
+    std::vector<double *> Jn(h->nmol, nullptr), Kn(h->nmol, nullptr);
+    try {
+        return build_impl(h, D, n_dm, with_j, with_k, cutoff, precision_mode, J ? J : Jn.data(), K ? K : Kn.data(),
+                          stream, stats);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_OOM, "host exception: %s", e.what());
+    }
+}
+
+int jk_set_option(jk_handle *h, const char *key, double value)
+{
+    if (!h || !key) return fail(JK_ERR_ARG, "NULL handle or key");
+    std::string k = key;
+    if (k == "tau32") { if (!(value >= 0)) return fail(JK_ERR_ARG, "tau32 must be >= 0"); h->tau32 = value; }
+    else if (k == "router_band") { if (!(value >= 1)) return fail(JK_ERR_ARG, "router_band must be >= 1"); h->router_band = value; }
+    else if (k == "pair_cutoff") h->pair_cutoff = value;
+    else if (k == "use_graph") h->use_graph = value != 0;
+    else if (k == "use_dmax") h->use_dmax = value != 0;
+    else if (k == "profile") h->profile = value != 0;
+    else return fail(JK_ERR_ARG, "unknown option '%s'", key);
+    return JK_OK;
+}
+
+int jk_get_option(jk_handle *h, const char *key, double *value)
+{
+    if (!h || !key || !value) return fail(JK_ERR_ARG, "NULL argument");
+    std::string k = key;
+    if (k == "tau32") *value = h->tau32;
+    else if (k == "router_band") *value = h->router_band;
+    else if (k == "pair_cutoff") *value = h->pair_cutoff;
+    else if (k == "use_graph") *value = h->use_graph;
+    else if (k == "use_dmax") *value = h->use_dmax;
+    else if (k == "profile") *value = h->profile;
+    else if (k == "init_ms") *value = h->init_ms;
+    else if (k == "compile_ms") *value = h->compile_ms;
+    else if (k == "npairs") *value = (double)h->h_pairs.size();
+    else if (k == "nclasses") *value = (double)h->classes.size();
+    else if (k == "nlaunches") *value = (double)h->launches.size();
+    else return fail(JK_ERR_ARG, "unknown option '%s'", key);
+    return JK_OK;
+}
+
+int jk_info(jk_handle *h, int32_t mol, int32_t *nao, int32_t *nshell, int32_t *nmol)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    if (mol < 0 || mol >= h->nmol) return fail(JK_ERR_ARG, "molecule index out of range");
+    if (nao) *nao = h->nao_user[mol];
+    if (nshell) *nshell = h->mol_sh0[mol + 1] - h->mol_sh0[mol];
+    if (nmol) *nmol = h->nmol;
+    return JK_OK;
+}
+
+int jk_schwarz(jk_handle *h, double *Q)
+{
+    if (!h || !Q) return fail(JK_ERR_ARG, "NULL argument");
+    int ns = h->mol_sh0[1] - h->mol_sh0[0];
+    std::fill(Q, Q + (size_t)ns * ns, 0.0);
+    for (auto &p : h->h_pairs)
+        if (p.mol == 0) Q[(size_t)p.a_loc * ns + p.b_loc] = Q[(size_t)p.b_loc * ns + p.a_loc] = p.Q;
+    return JK_OK;
+}
+
+int jk_destroy(jk_handle *h)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    cudaDeviceSynchronize();
+    free_handle(h);
+    return JK_OK;
+}
+
+int jk_profile(jk_handle *h, jk_launch_prof *out, int32_t max, int32_t *n)
+{
+    if (!h || !n || (max > 0 && !out)) return fail(JK_ERR_ARG, "NULL argument");
+    int32_t c = (int32_t)std::min<size_t>(h->prof.size(), (size_t)std::max(0, max));
+    for (int32_t i = 0; i < c; ++i) out[i] = h->prof[i];
+    *n = (int32_t)h->prof.size();
+    return JK_OK;
+}
+
+int jk_measure_peak(int32_t which, double ms, double *flops_per_s)
+{
+    if (!flops_per_s || (which != 0 && which != 1) || !(ms > 0)) return fail(JK_ERR_ARG, "bad argument");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    void *sink = nullptr;
+    CK(cudaMalloc(&sink, 16));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int threads = 256, blocks = sms * 8;
+    auto run = [&](int iters) -> float {
+        cudaEventRecord(e0);
+        if (which == 0) jk_fma_probe_kernel<double><<<blocks, threads>>>(iters, 1.0, (double *)sink);
+        else jk_fma_probe_kernel<float><<<blocks, threads>>>(iters, 1.0f, (float *)sink);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        return t;
+    };
+    int iters = 64;
+    run(iters);
+    float t = run(iters);
+    while (t < ms && iters < (1 << 26)) { iters *= 2; t = run(iters); }
+    t = run(iters);
+    double flops = 2.0 * 8 * 16 * (double)iters * threads * blocks;
+    *flops_per_s = flops / (t * 1e-3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    CK(cudaGetLastError());
+    return JK_OK;
+}
+
+int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na, int32_t nb, int32_t nc,
+                     int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32,
+                     int32_t *threads_per_quartet, double *compile_ms)
+{
+    if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > JK_LMAX || lb > JK_LMAX || lc > JK_LMAX || ld > JK_LMAX)
+        return fail(JK_ERR_UNSUPPORTED, "angular momentum out of range");
+    if (na < 1 || nb < 1 || nc < 1 || nd < 1 || na > JK_NPRIM_MAX || nb > JK_NPRIM_MAX || nc > JK_NPRIM_MAX ||
+        nd > JK_NPRIM_MAX)
+        return fail(JK_ERR_UNSUPPORTED, "primitive count out of range");
+    if (n_dm < 1 || n_dm > JK_NDM_MAX || (!with_j && !with_k)) return fail(JK_ERR_ARG, "bad n_dm or flags");
+    KSpec s;
+    s.kind = 0;
+    s.la = la; s.lb = lb; s.lc = lc; s.ld = ld; s.na = na; s.nb = nb; s.nc = nc; s.nd = nd;
+    s.ndm = n_dm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0; s.fp32 = fp32 ? 1 : 0;
+    choose_fragments(s, false);
+    if (threads_per_quartet) *threads_per_quartet = s.G();
+    try {
+        return compile_to_disk({s}, compile_ms);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_COMPILE, "host exception: %s", e.what());
+    }
+}
+
+const char *jk_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,611 @@
+// Integral kernels of the JK build, compiled at run time by NVRTC for
+// sm_103a, one instantiation per (l_a, l_b, l_c, l_d, n_a, n_b, n_c, n_d)
+// class and per fragmentation, density count, J/K flags and precision
+// (the static parameters of Table 1 of the paper). The library prepends
+// jk_types.h and the generated rys_params.cuh.
+//
+// Method (Sec. 2 of the paper):
+//   eq:rys0  (ab|cd) = sum over primitive quartets of c_a c_b c_c c_d (pq|rs)
+//   eq:rys1  (pq|rs) = sum_r w_r (pq|rs)(t_r), N_r = floor(L/2) + 1 roots
+//   eq:rys2  (pq|rs)(t_r) = I_x I_y I_z, each a 2D table over the Cartesian
+//            exponents of the four centres, built per root by the vertical
+//            recurrence on (A, C) and the horizontal transfers A->B, C->D
+//   eq:jk    J_ab += T D_cd, J_cd += T D_ab, K_ac += T D_bd, K_ad += T D_bc,
+//            K_bc += T D_ad, K_bd += T D_ac for each unique quartet (8-fold
+//            symmetry, Sec. 2), scaled by the degeneracy factor f: 2f for J
+//            and f for K into half matrices that are symmetrised afterwards.
+//
+// Thread mapping: a group of G = GA*GB*GC*GD threads evaluates one shell
+// quartet. Each thread owns a fragment of FA x FB x FC x FD Cartesian
+// components (the 1qnt fragmentation of Sec. 3.2; G = 1 is the 1q1t case of
+// Sec. 3.1). With G == 1 the 2D tables live in registers; with G > 1 they
+// live in shared memory, one set per group, built cooperatively per root and
+// direction. A warp owns one bra pair at a time and scans its ket pairs in
+// chunks of 32 candidates, screening each (Schwarz times density-block max),
+// so the quartet list is never materialised; the J_ab partial stays in
+// registers across the whole ket scan and is flushed once per bra pair.
+
+#define JK_TWO_PI_2_5 34.986836655249725  // 2 pi^(5/2)
+
+__device__ constexpr int jk_ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// Cartesian exponent along `axis` of component idx of a shell with angular
+// momentum l: components ordered x descending, then y descending.
+__device__ constexpr int jk_cart_exp(int l, int idx, int axis)
+{
+    int k = 0;
+    for (int x = l; x >= 0; --x)
+        for (int y = l - x; y >= 0; --y) {
+            if (k == idx) return axis == 0 ? x : (axis == 1 ? y : l - x - y);
+            ++k;
+        }
+    return 0;
+}
+
+template <typename R> struct JkPP;
+template <> struct JkPP<double> { typedef JkPrimPair64 T; };
+template <> struct JkPP<float> { typedef JkPrimPair32 T; };
+
+__device__ __forceinline__ double jk_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float jk_rsqrt(float x) { return rsqrtf(x); }
+
+// ----------------------------------------------------- Rys roots, weights
+// Root r and weight r of the N-point rule at T. The piecewise polynomials
+// cover 0 <= T < tmax; above it the half-range Gauss-Hermite limit
+// u = x^2 / T, w = w_h / sqrt(T) holds (evaluated in FP64 in both tiers).
+template <int N>
+__device__ __forceinline__ void jk_rys_one(double T, int r, const double *__restrict__ tab,
+                                           double &u, double &w)
+{
+    if (T >= rys64_tmax[N]) {
+        double s = rsqrt(T);
+        u = rys_gh[rys_gh_offset[N - 1] + r] * (s * s);
+        w = rys_gh[rys_gh_offset[N - 1] + N + r] * s;
+        return;
+    }
+    int k = min((int)(T * RYS64_INVH), rys64_nint[N] - 1);
+    double x = (T - k * RYS64_H) * (2.0 * RYS64_INVH) - 1.0;
+    const double *cu = tab + rys64_offset[N] + (long long)k * (2 * N * (RYS64_DEG + 1)) + r * (RYS64_DEG + 1);
+    const double *cw = cu + N * (RYS64_DEG + 1);
+    double au = __ldg(cu + RYS64_DEG), aw = __ldg(cw + RYS64_DEG);
+#pragma unroll
+    for (int i = RYS64_DEG - 1; i >= 0; --i) {
+        au = fma(au, x, __ldg(cu + i));
+        aw = fma(aw, x, __ldg(cw + i));
+    }
+    u = au;
+    w = aw;
+}
+
+template <int N>
+__device__ __forceinline__ void jk_rys_one(float T, int r, const float *__restrict__ tab,
+                                           float &u, float &w)
+{
+    if (T >= (float)rys32_tmax[N]) {
+        double Td = T;
+        double s = rsqrt(Td);
+        u = (float)(rys_gh[rys_gh_offset[N - 1] + r] * (s * s));
+        w = (float)(rys_gh[rys_gh_offset[N - 1] + N + r] * s);
+        return;
+    }
+    int k = min((int)(T * (float)RYS32_INVH), rys32_nint[N] - 1);
+    float x = (T - k * (float)RYS32_H) * (float)(2.0 * RYS32_INVH) - 1.0f;
+    const float *cu = tab + rys32_offset[N] + k * (2 * N * (RYS32_DEG + 1)) + r * (RYS32_DEG + 1);
+    const float *cw = cu + N * (RYS32_DEG + 1);
+    float au = __ldg(cu + RYS32_DEG), aw = __ldg(cw + RYS32_DEG);
+#pragma unroll
+    for (int i = RYS32_DEG - 1; i >= 0; --i) {
+        au = fmaf(au, x, __ldg(cu + i));
+        aw = fmaf(aw, x, __ldg(cw + i));
+    }
+    u = au;
+    w = aw;
+}
+
+// --------------------------------------------------------- 2D integrals
+// One direction, one root: vertical recurrence on (n on A, m on C) up to
+// (LA+LB, LC+LD), then horizontal transfers to (a, b, c, d). Output layout
+// out[((a*(LB+1) + b)*(LC+1) + c)*(LD+1) + d].
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void jk_build_2d(R c00, R c00p, R b10, R b01, R b00, R i00,
+                                            R ab, R cd, R *__restrict__ out)
+{
+    constexpr int NA = LA + LB, NC = LC + LD;
+    R V[NA + 1][NC + 1];
+    V[0][0] = i00;
+    if (NA > 0) V[1][0] = c00 * i00;
+#pragma unroll
+    for (int n = 1; n < NA; ++n) V[n + 1][0] = c00 * V[n][0] + R(n) * b10 * V[n - 1][0];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+#pragma unroll
+        for (int n = 0; n <= NA; ++n) {
+            R v = c00p * V[n][m];
+            if (m > 0) v += R(m) * b01 * V[n][m - 1];
+            if (n > 0) v += R(n) * b00 * V[n - 1][m];
+            V[n][m + 1] = v;
+        }
+    }
+    // bra transfer A -> B: H[a][b] = H[a+1][b-1] + AB H[a][b-1]
+    R HB[LA + 1][LB + 1][NC + 1];
+#pragma unroll
+    for (int m = 0; m <= NC; ++m) {
+        R t[NA + 1][LB + 1];
+#pragma unroll
+        for (int n = 0; n <= NA; ++n) t[n][0] = V[n][m];
+#pragma unroll
+        for (int b = 1; b <= LB; ++b)
+#pragma unroll
+            for (int a = 0; a <= NA - b; ++a) t[a][b] = t[a + 1][b - 1] + ab * t[a][b - 1];
+#pragma unroll
+        for (int a = 0; a <= LA; ++a)
+#pragma unroll
+            for (int b = 0; b <= LB; ++b) HB[a][b][m] = t[a][b];
+    }
+    // ket transfer C -> D
+#pragma unroll
+    for (int a = 0; a <= LA; ++a)
+#pragma unroll
+        for (int b = 0; b <= LB; ++b) {
+            R s[NC + 1][LD + 1];
+#pragma unroll
+            for (int m = 0; m <= NC; ++m) s[m][0] = HB[a][b][m];
+#pragma unroll
+            for (int d = 1; d <= LD; ++d)
+#pragma unroll
+                for (int c = 0; c <= NC - d; ++c) s[c][d] = s[c + 1][d - 1] + cd * s[c][d - 1];
+#pragma unroll
+            for (int c = 0; c <= LC; ++c)
+#pragma unroll
+                for (int d = 0; d <= LD; ++d) out[((a * (LB + 1) + b) * (LC + 1) + c) * (LD + 1) + d] = s[c][d];
+        }
+}
+
+// ----------------------------------------------------------- class shape
+template <int LA, int LB, int LC, int LD, int GA, int GB, int GC, int GD>
+struct JkShape {
+    static constexpr int NFA = jk_ncart(LA), NFB = jk_ncart(LB), NFC = jk_ncart(LC), NFD = jk_ncart(LD);
+    static constexpr int FA = NFA / GA, FB = NFB / GB, FC = NFC / GC, FD = NFD / GD;
+    static constexpr int G = GA * GB * GC * GD;
+    static constexpr int EPT = FA * FB * FC * FD;
+    static constexpr int L = LA + LB + LC + LD;
+    static constexpr int NR = L / 2 + 1;
+    static constexpr int SD = 1, SC = LD + 1, SB = (LC + 1) * (LD + 1), SA = (LB + 1) * SB;
+    static constexpr int NI = (LA + 1) * SA;
+    // reals of shared memory per group (G > 1): 2D tables and the roots
+    static constexpr int SMEM_GROUP = (G == 1) ? 0 : (NR * 3 * NI + 2 * NR);
+    static_assert(NFA % GA == 0 && NFB % GB == 0 && NFC % GC == 0 && NFD % GD == 0, "fragment");
+    static_assert(G <= 32, "groups are warp-local");
+};
+
+// Offsets into a 2D table for the components a thread owns (G > 1).
+template <class S>
+struct JkOffsets {
+    int a[3][S::FA], b[3][S::FB], c[3][S::FC], d[3][S::FD];
+};
+
+template <int LA, int LB, int LC, int LD, int GA, int GB, int GC, int GD>
+__device__ __forceinline__ void jk_make_offsets(int ga, int gb, int gc, int gd,
+                                                JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD>> &o)
+{
+    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+        for (int i = 0; i < S::FA; ++i) {
+            int idx = ga * S::FA + i, e = 0, k = 0;
+            for (int x = LA; x >= 0; --x)
+                for (int y = LA - x; y >= 0; --y, ++k)
+                    if (k == idx) e = ax == 0 ? x : (ax == 1 ? y : LA - x - y);
+            o.a[ax][i] = e * S::SA;
+        }
+#pragma unroll
+        for (int i = 0; i < S::FB; ++i) {
+            int idx = gb * S::FB + i, e = 0, k = 0;
+            for (int x = LB; x >= 0; --x)
+                for (int y = LB - x; y >= 0; --y, ++k)
+                    if (k == idx) e = ax == 0 ? x : (ax == 1 ? y : LB - x - y);
+            o.b[ax][i] = e * S::SB;
+        }
+#pragma unroll
+        for (int i = 0; i < S::FC; ++i) {
+            int idx = gc * S::FC + i, e = 0, k = 0;
+            for (int x = LC; x >= 0; --x)
+                for (int y = LC - x; y >= 0; --y, ++k)
+                    if (k == idx) e = ax == 0 ? x : (ax == 1 ? y : LC - x - y);
+            o.c[ax][i] = e * S::SC;
+        }
+#pragma unroll
+        for (int i = 0; i < S::FD; ++i) {
+            int idx = gd * S::FD + i, e = 0, k = 0;
+            for (int x = LD; x >= 0; --x)
+                for (int y = LD - x; y >= 0; --y, ++k)
+                    if (k == idx) e = ax == 0 ? x : (ax == 1 ? y : LD - x - y);
+            o.d[ax][i] = e * S::SD;
+        }
+    }
+}
+
+// ------------------------------------------------ one contracted quartet
+// Accumulates the thread's fragment T[EPT] of the contracted block (ab|cd)
+// over every primitive quartet (eq:rys0). `grp` is the group's shared
+// memory (G > 1), gmask the group's lane mask.
+template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
+          int GA, int GB, int GC, int GD, typename R>
+__device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
+                                           const typename JkPP<R>::T *__restrict__ pp,
+                                           const R *__restrict__ rys, R *grp, unsigned gmask, int tg,
+                                           const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD>> &off,
+                                           R (&T)[JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::EPT])
+{
+    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
+    typedef typename JkPP<R>::T PPT;
+    constexpr int NR = S::NR;
+    const R ABx = (R)bra.ABx, ABy = (R)bra.ABy, ABz = (R)bra.ABz;
+    const R CDx = (R)ket.ABx, CDy = (R)ket.ABy, CDz = (R)ket.ABz;
+    const PPT *bpp = pp + bra.pp_off;
+    const PPT *kpp = pp + ket.pp_off;
+#pragma unroll 1
+    for (int ij = 0; ij < NPA * NPB; ++ij) {
+        const PPT bp = bpp[ij];
+        for (int kl = 0; kl < NPC * NPD; ++kl) {
+            const PPT kp = kpp[kl];
+            const R p = bp.p, q = kp.p;
+            const R rpq = jk_rsqrt(p + q);
+            const R inv_pq = rpq * rpq;
+            const R PQx = bp.Px - kp.Px, PQy = bp.Py - kp.Py, PQz = bp.Pz - kp.Pz;
+            const R rho = p * q * inv_pq;
+            const R Tt = rho * (PQx * PQx + PQy * PQy + PQz * PQz);
+            const R pref = (R)JK_TWO_PI_2_5 * bp.K * kp.K * rpq;
+            const R qf = q * inv_pq, pf = p * inv_pq;
+            if (S::G == 1) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    R u, w;
+                    jk_rys_one<NR>(Tt, r, rys, u, w);
+                    const R b00 = (R)0.5 * u * inv_pq;
+                    const R b10 = bp.inv2p * ((R)1 - u * qf);
+                    const R b01 = kp.inv2p * ((R)1 - u * pf);
+                    const R uq = u * qf, up = u * pf;
+                    R tx[S::NI], ty[S::NI], tz[S::NI];
+                    jk_build_2d<LA, LB, LC, LD, R>(bp.PAx - uq * PQx, kp.PAx + up * PQx, b10, b01, b00, (R)1, ABx, CDx, tx);
+                    jk_build_2d<LA, LB, LC, LD, R>(bp.PAy - uq * PQy, kp.PAy + up * PQy, b10, b01, b00, (R)1, ABy, CDy, ty);
+                    jk_build_2d<LA, LB, LC, LD, R>(bp.PAz - uq * PQz, kp.PAz + up * PQz, b10, b01, b00, w * pref, ABz, CDz, tz);
+#pragma unroll
+                    for (int ia = 0; ia < S::FA; ++ia)
+#pragma unroll
+                        for (int ib = 0; ib < S::FB; ++ib)
+#pragma unroll
+                            for (int ic = 0; ic < S::FC; ++ic)
+#pragma unroll
+                                for (int id = 0; id < S::FD; ++id) {
+                                    const int ox = jk_cart_exp(LA, ia, 0) * S::SA + jk_cart_exp(LB, ib, 0) * S::SB +
+                                                   jk_cart_exp(LC, ic, 0) * S::SC + jk_cart_exp(LD, id, 0);
+                                    const int oy = jk_cart_exp(LA, ia, 1) * S::SA + jk_cart_exp(LB, ib, 1) * S::SB +
+                                                   jk_cart_exp(LC, ic, 1) * S::SC + jk_cart_exp(LD, id, 1);
+                                    const int oz = jk_cart_exp(LA, ia, 2) * S::SA + jk_cart_exp(LB, ib, 2) * S::SB +
+                                                   jk_cart_exp(LC, ic, 2) * S::SC + jk_cart_exp(LD, id, 2);
+                                    const int k = ((ia * S::FB + ib) * S::FC + ic) * S::FD + id;
+                                    T[k] += tx[ox] * ty[oy] * tz[oz];
+                                }
+                }
+            } else {
+                R *roots = grp + NR * 3 * S::NI;   // [0, NR): u ; [NR, 2NR): w * pref
+                if (tg < NR) {
+                    R u, w;
+                    jk_rys_one<NR>(Tt, tg, rys, u, w);
+                    roots[tg] = u;
+                    roots[NR + tg] = w * pref;
+                }
+                __syncwarp(gmask);
+                for (int task = tg; task < 3 * NR; task += S::G) {
+                    const int r = task / 3, dir = task - 3 * r;
+                    const R u = roots[r];
+                    const R b00 = (R)0.5 * u * inv_pq;
+                    const R b10 = bp.inv2p * ((R)1 - u * qf);
+                    const R b01 = kp.inv2p * ((R)1 - u * pf);
+                    const R uq = u * qf, up = u * pf;
+                    R pa, qc, pqd, abd, cdd, i00 = (R)1;
+                    if (dir == 0) { pa = bp.PAx; qc = kp.PAx; pqd = PQx; abd = ABx; cdd = CDx; }
+                    else if (dir == 1) { pa = bp.PAy; qc = kp.PAy; pqd = PQy; abd = ABy; cdd = CDy; }
+                    else { pa = bp.PAz; qc = kp.PAz; pqd = PQz; abd = ABz; cdd = CDz; i00 = roots[NR + r]; }
+                    jk_build_2d<LA, LB, LC, LD, R>(pa - uq * pqd, qc + up * pqd, b10, b01, b00, i00, abd, cdd,
+                                                   grp + (r * 3 + dir) * S::NI);
+                }
+                __syncwarp(gmask);
+#pragma unroll
+                for (int ia = 0; ia < S::FA; ++ia)
+#pragma unroll
+                    for (int ib = 0; ib < S::FB; ++ib)
+#pragma unroll
+                        for (int ic = 0; ic < S::FC; ++ic)
+#pragma unroll
+                            for (int id = 0; id < S::FD; ++id) {
+                                const int ox = off.a[0][ia] + off.b[0][ib] + off.c[0][ic] + off.d[0][id];
+                                const int oy = off.a[1][ia] + off.b[1][ib] + off.c[1][ic] + off.d[1][id];
+                                const int oz = off.a[2][ia] + off.b[2][ib] + off.c[2][ic] + off.d[2][id];
+                                const int k = ((ia * S::FB + ib) * S::FC + ic) * S::FD + id;
+                                R acc = (R)0;
+#pragma unroll
+                                for (int r = 0; r < NR; ++r)
+                                    acc += grp[(r * 3 + 0) * S::NI + ox] * grp[(r * 3 + 1) * S::NI + oy] *
+                                           grp[(r * 3 + 2) * S::NI + oz];
+                                T[k] += acc;
+                            }
+                __syncwarp(gmask);
+            }
+        }
+    }
+}
+
+template <typename R> __device__ __forceinline__ const typename JkPP<R>::T *jk_pp(const JkClassArgs &a);
+template <> __device__ __forceinline__ const JkPrimPair64 *jk_pp<double>(const JkClassArgs &a) { return a.pp64; }
+template <> __device__ __forceinline__ const JkPrimPair32 *jk_pp<float>(const JkClassArgs &a) { return a.pp32; }
+template <typename R> __device__ __forceinline__ const R *jk_rys(const JkClassArgs &a);
+template <> __device__ __forceinline__ const double *jk_rys<double>(const JkClassArgs &a) { return a.rys64; }
+template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassArgs &a) { return a.rys32; }
+
+// ------------------------------------------------------- the class kernel
+template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
+          int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R>
+__global__ void __launch_bounds__(128) jk_class_kernel(const JkClassArgs args)
+{
+    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
+    constexpr int G = S::G, NGW = 32 / G;
+    constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
+    extern __shared__ double jk_smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gw = lane / G, tg = lane - gw * G;
+    const bool active = gw < NGW;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gw * G));
+    R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
+    // fragment coordinates of this thread inside its group
+    const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
+    JkOffsets<S> off;
+    jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+    const typename JkPP<R>::T *pp = jk_pp<R>(args);
+    const R *rys = jk_rys<R>(args);
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(args.work, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= args.nbra) break;
+        const JkPair bra = args.bra[item];
+        const JkMol mol = args.mols[bra.mol];
+        const int kb = args.same_class ? item : args.ket_beg[bra.mol];
+        const int ke = args.ket_end[bra.mol];
+        const double *dmx = args.dmax + mol.dmax_off;
+        const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
+        const long long nn = (long long)mol.nao * mol.nao;
+        const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+        R jab[NDM][FA][FB];
+#pragma unroll
+        for (int m = 0; m < NDM; ++m)
+#pragma unroll
+            for (int i = 0; i < FA; ++i)
+#pragma unroll
+                for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
+        unsigned long long nq = 0;
+
+        for (int base = kb; base < ke; base += 32) {
+            const int j = base + lane;
+            bool sig = false, stop = false;
+            if (j < ke) {
+                const double bq = bra.Q * args.ket[j].Q;
+                if (bq * dmol <= args.lo) {
+                    stop = true;
+                } else {
+                    double dm = 1.0;
+                    if (args.use_dmax) {
+                        const int c = args.ket[j].a_loc, d = args.ket[j].b_loc;
+                        const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
+                        dm = 0.0;
+                        if (args.with_j) dm = fmax(__ldg(dmx + a * ns + b), __ldg(dmx + c * ns + d));
+                        if (args.with_k) {
+                            dm = fmax(dm, fmax(__ldg(dmx + a * ns + c), __ldg(dmx + a * ns + d)));
+                            dm = fmax(dm, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
+                        }
+                    }
+                    const double B = bq * dm;
+                    sig = (B > args.lo) && (B <= args.hi);
+                }
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, sig);
+            nq += __popc(mask);
+            while (mask) {
+                int myket = -1;
+                if (active) {
+                    unsigned m = mask;
+                    for (int s = 0; s < gw && m; ++s) m &= m - 1;
+                    if (m) myket = base + __ffs(m) - 1;
+                }
+#pragma unroll 1
+                for (int s = 0; s < NGW && mask; ++s) mask &= mask - 1;
+                if (myket >= 0) {
+                    const JkPair ket = args.ket[myket];
+                    R T[S::EPT];
+#pragma unroll
+                    for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
+                    jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(bra, ket, pp, rys, grp, gmask, tg, off, T);
+                    R f = (R)1;
+                    if (bra.a == bra.b) f *= (R)0.5;
+                    if (ket.a == ket.b) f *= (R)0.5;
+                    if (args.same_class && myket == item) f *= (R)0.5;
+                    const int c0 = ket.a_ao + gc * FC, d0 = ket.b_ao + gd * FD;
+#pragma unroll
+                    for (int m = 0; m < NDM; ++m) {
+                        const double *D = mol.D + m * nn;
+                        const int nao = mol.nao;
+                        if (DOJ) {
+                            R Dcd[FC][FD], Dab[FA][FB];
+#pragma unroll
+                            for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                                for (int id = 0; id < FD; ++id) Dcd[ic][id] = (R)__ldg(D + (long long)(c0 + ic) * nao + d0 + id);
+#pragma unroll
+                            for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                                for (int ib = 0; ib < FB; ++ib) Dab[ia][ib] = (R)__ldg(D + (long long)(a0 + ia) * nao + b0 + ib);
+                            R jcd[FC][FD];
+#pragma unroll
+                            for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                                for (int id = 0; id < FD; ++id) jcd[ic][id] = (R)0;
+#pragma unroll
+                            for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                                for (int ib = 0; ib < FB; ++ib) {
+                                    R s = (R)0;
+#pragma unroll
+                                    for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                                        for (int id = 0; id < FD; ++id) {
+                                            const R t = T[((ia * FB + ib) * FC + ic) * FD + id];
+                                            s += t * Dcd[ic][id];
+                                            jcd[ic][id] += t * Dab[ia][ib];
+                                        }
+                                    jab[m][ia][ib] += (R)2 * f * s;
+                                }
+#pragma unroll
+                            for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                                for (int id = 0; id < FD; ++id)
+                                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, (double)((R)2 * f * jcd[ic][id]));
+                        }
+                        if (DOK) {
+                            R Dbd[FB][FD], Dbc[FB][FC], Dad[FA][FD], Dac[FA][FC];
+#pragma unroll
+                            for (int ib = 0; ib < FB; ++ib) {
+#pragma unroll
+                                for (int id = 0; id < FD; ++id) Dbd[ib][id] = (R)__ldg(D + (long long)(b0 + ib) * nao + d0 + id);
+#pragma unroll
+                                for (int ic = 0; ic < FC; ++ic) Dbc[ib][ic] = (R)__ldg(D + (long long)(b0 + ib) * nao + c0 + ic);
+                            }
+#pragma unroll
+                            for (int ia = 0; ia < FA; ++ia) {
+#pragma unroll
+                                for (int id = 0; id < FD; ++id) Dad[ia][id] = (R)__ldg(D + (long long)(a0 + ia) * nao + d0 + id);
+#pragma unroll
+                                for (int ic = 0; ic < FC; ++ic) Dac[ia][ic] = (R)__ldg(D + (long long)(a0 + ia) * nao + c0 + ic);
+                            }
+                            R kac[FA][FC], kad[FA][FD], kbc[FB][FC], kbd[FB][FD];
+#pragma unroll
+                            for (int ia = 0; ia < FA; ++ia) {
+#pragma unroll
+                                for (int ic = 0; ic < FC; ++ic) kac[ia][ic] = (R)0;
+#pragma unroll
+                                for (int id = 0; id < FD; ++id) kad[ia][id] = (R)0;
+                            }
+#pragma unroll
+                            for (int ib = 0; ib < FB; ++ib) {
+#pragma unroll
+                                for (int ic = 0; ic < FC; ++ic) kbc[ib][ic] = (R)0;
+#pragma unroll
+                                for (int id = 0; id < FD; ++id) kbd[ib][id] = (R)0;
+                            }
+#pragma unroll
+                            for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                                for (int ib = 0; ib < FB; ++ib)
+#pragma unroll
+                                    for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                                        for (int id = 0; id < FD; ++id) {
+                                            const R t = T[((ia * FB + ib) * FC + ic) * FD + id];
+                                            kac[ia][ic] += t * Dbd[ib][id];
+                                            kad[ia][id] += t * Dbc[ib][ic];
+                                            kbc[ib][ic] += t * Dad[ia][id];
+                                            kbd[ib][id] += t * Dac[ia][ic];
+                                        }
+                            double *K = mol.K + m * nn;
+#pragma unroll
+                            for (int ia = 0; ia < FA; ++ia) {
+#pragma unroll
+                                for (int ic = 0; ic < FC; ++ic)
+                                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, (double)(f * kac[ia][ic]));
+#pragma unroll
+                                for (int id = 0; id < FD; ++id)
+                                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, (double)(f * kad[ia][id]));
+                            }
+#pragma unroll
+                            for (int ib = 0; ib < FB; ++ib) {
+#pragma unroll
+                                for (int ic = 0; ic < FC; ++ic)
+                                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, (double)(f * kbc[ib][ic]));
+#pragma unroll
+                                for (int id = 0; id < FD; ++id)
+                                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, (double)(f * kbd[ib][id]));
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (__any_sync(0xffffffffu, stop)) break;
+        }
+        if (DOJ && active) {
+#pragma unroll
+            for (int m = 0; m < NDM; ++m)
+#pragma unroll
+                for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                    for (int ib = 0; ib < FB; ++ib)
+                        if (jab[m][ia][ib] != (R)0)
+                            atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, (double)jab[m][ia][ib]);
+        }
+        if (lane == 0 && nq) {
+            atomicAdd(args.stats, nq);
+            atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+        }
+    }
+}
+
+// ------------------------------------------------- Schwarz factors Q_ab
+// Diagonal quartets (ab|ab) of one pair class in FP64; Q_ab is the square
+// root of the largest |(mu nu|mu nu)| (eq:schwartz at shell level).
+template <int LA, int LB, int NPA, int NPB, int GA, int GB, int GC, int GD>
+__global__ void __launch_bounds__(128) jk_schwarz_kernel(const JkSchwarzArgs args)
+{
+    typedef JkShape<LA, LB, LA, LB, GA, GB, GC, GD> S;
+    static_assert(GA == GC && GB == GD, "diagonal elements must stay inside one thread");
+    constexpr int G = S::G, NGW = 32 / G;
+    constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
+    extern __shared__ double jk_smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gw = lane / G, tg = lane - gw * G;
+    const bool active = gw < NGW;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gw * G));
+    double *grp = jk_smem_raw + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
+    const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
+    JkOffsets<S> off;
+    jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+    const int warps_total = (gridDim.x * blockDim.x) >> 5;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int base = gwarp * NGW; base < args.npair; base += warps_total * NGW) {
+        const int pi = base + gw;
+        const bool mine = active && pi < args.npair;
+        double mx = 0.0;
+        if (mine) {
+            const JkPair pr = args.pairs[pi];
+            double T[S::EPT];
+#pragma unroll
+            for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
+            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, args.pp64, args.rys64, grp, gmask, tg, off, T);
+            if (ga == gc && gb == gd) {
+#pragma unroll
+                for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                    for (int ib = 0; ib < FB; ++ib)
+                        mx = fmax(mx, fabs(T[((ia * FB + ib) * FC + ia) * FD + ib]));
+            }
+        }
+        // group max through the group's lanes
+        double gmx = mx;
+        for (int s = 0; s < G; ++s) gmx = fmax(gmx, __shfl_sync(0xffffffffu, mx, (gw * G + s) & 31));
+        if (mine && tg == 0) args.Qout[pi] = sqrt(gmx);
+        __syncwarp();
+    }
+}

@@ -1,0 +1,82 @@
+// Plain-data records shared by the host planner (nvcc/g++) and the
+// runtime-compiled integral kernels (NVRTC). No includes: NVRTC compiles this
+// file without the CUDA toolkit headers.
+#pragma once
+
+// One significant shell pair (a, b), oriented so that the shell type of a
+// (l, then nprim) is >= that of b. Pairs of one pair class are stored
+// contiguously, grouped by molecule and sorted by descending Q inside a
+// molecule, so that a ket scan can stop at the first Q that fails the bound.
+struct JkPair {
+    int a, b;          // global shell indices
+    int mol;           // molecule index
+    int pp_off;        // first primitive pair (na*nb of them, a-major)
+    int a_ao, b_ao;    // molecule-local Cartesian AO offsets
+    int a_loc, b_loc;  // molecule-local shell indices (density-max table)
+    double Q;          // Schwarz factor sqrt(max |(mu nu|mu nu)|)
+    double Ax, Ay, Az; // centre of shell a
+    double ABx, ABy, ABz;  // A - B (horizontal recurrence)
+    double pad;
+};
+
+// Per primitive pair (alpha_i on a, beta_j on b), p = alpha + beta:
+//   P    = (alpha A + beta B) / p
+//   PA   = P - A
+//   K    = c_i c_j exp(-alpha beta |A-B|^2 / p) / p
+//   inv2p = 1 / (2 p)
+struct JkPrimPair64 {
+    double Px, Py, Pz, p;
+    double PAx, PAy, PAz, K;
+    double inv2p, pad0, pad1, pad2;
+};
+struct JkPrimPair32 {
+    float Px, Py, Pz, p;
+    float PAx, PAy, PAz, K;
+    float inv2p, pad0, pad1, pad2;
+};
+
+// Per molecule of a handle.
+struct JkMol {
+    const double *D;   // n_dm x nao x nao (Cartesian)
+    double *J;         // half-matrix accumulator X, symmetrised after the build
+    double *K;         // half-matrix accumulator Y
+    int nao;           // Cartesian functions
+    int nsh;           // shells
+    long long dmax_off;  // offset of this molecule's nsh x nsh block-max table
+};
+
+// Arguments of one class-pair launch (passed by value).
+struct JkClassArgs {
+    const JkPair *bra;           // pairs of the bra class
+    const JkPair *ket;           // pairs of the ket class
+    const int *ket_beg;          // per molecule: first ket index in the ket class
+    const int *ket_end;          // per molecule: one past the last
+    const JkPrimPair64 *pp64;
+    const JkPrimPair32 *pp32;
+    const JkMol *mols;
+    const double *dmax;          // block max |D| tables, all molecules
+    const double *dmax_mol;      // per molecule: max over its table
+    const double *rys64;         // FP64 Rys tables
+    const float *rys32;          // FP32 Rys tables
+    int *work;                   // work counter (zeroed before the launch)
+    unsigned long long *stats;   // [0] quartets, [1] primitive quartets
+    int *err;                    // device error word
+    double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi
+    int nbra;
+    int same_class;              // ket class == bra class: ket index >= bra index
+    int with_j, with_k;          // which outputs (and density blocks) to use
+    int use_dmax;                // 0: screen with Dmax := 1
+    int ndm;
+};
+
+// Arguments of the Schwarz (diagonal-quartet) launch of one pair class.
+struct JkSchwarzArgs {
+    const JkPair *pairs;
+    const JkPrimPair64 *pp64;
+    const double *rys64;
+    double *Qout;                // one per pair
+    int npair;
+};
+
+#define JK_ERR_DEV_TIMEOUT 1
+#define JK_ERR_DEV_BOUNDS 2

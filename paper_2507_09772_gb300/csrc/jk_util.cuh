@@ -1,0 +1,137 @@
+// Small device kernels of the JK build compiled ahead of time by nvcc:
+// primitive-pair tables, density block maxima, zeroing and symmetrisation.
+#pragma once
+#include "jk_types.h"
+
+// Primitive-pair records of one shell pair per thread (Sec. 3, pair data
+// precomputed once per geometry; Table 2 lists the raw inputs).
+__global__ void jk_pairdata_kernel(int npair, const int *__restrict__ pa, const int *__restrict__ pb,
+                                   const int *__restrict__ pp_off, const int *__restrict__ sh_atom,
+                                   const int *__restrict__ sh_nprim, const int *__restrict__ sh_prim,
+                                   const double *__restrict__ coords, const double *__restrict__ exps,
+                                   const double *__restrict__ coeffs, JkPrimPair64 *__restrict__ out64,
+                                   JkPrimPair32 *__restrict__ out32)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npair) return;
+    const int a = pa[t], b = pb[t];
+    const double *A = coords + 3 * sh_atom[a], *B = coords + 3 * sh_atom[b];
+    const double ABx = A[0] - B[0], ABy = A[1] - B[1], ABz = A[2] - B[2];
+    const double r2 = ABx * ABx + ABy * ABy + ABz * ABz;
+    const int na = sh_nprim[a], nb = sh_nprim[b];
+    int o = pp_off[t];
+    for (int i = 0; i < na; ++i) {
+        const double al = exps[sh_prim[a] + i], ca = coeffs[sh_prim[a] + i];
+        for (int j = 0; j < nb; ++j, ++o) {
+            const double be = exps[sh_prim[b] + j], cb = coeffs[sh_prim[b] + j];
+            const double p = al + be, ip = 1.0 / p;
+            JkPrimPair64 r;
+            r.Px = (al * A[0] + be * B[0]) * ip;
+            r.Py = (al * A[1] + be * B[1]) * ip;
+            r.Pz = (al * A[2] + be * B[2]) * ip;
+            r.p = p;
+            r.PAx = r.Px - A[0];
+            r.PAy = r.Py - A[1];
+            r.PAz = r.Pz - A[2];
+            r.K = ca * cb * exp(-al * be * ip * r2) * ip;
+            r.inv2p = 0.5 * ip;
+            r.pad0 = r.pad1 = r.pad2 = 0.0;
+            out64[o] = r;
+            JkPrimPair32 s;
+            s.Px = (float)r.Px; s.Py = (float)r.Py; s.Pz = (float)r.Pz; s.p = (float)p;
+            s.PAx = (float)r.PAx; s.PAy = (float)r.PAy; s.PAz = (float)r.PAz; s.K = (float)r.K;
+            s.inv2p = (float)r.inv2p; s.pad0 = s.pad1 = s.pad2 = 0.f;
+            out32[o] = s;
+        }
+    }
+}
+
+// Block-max |D| over every density: one CTA per (molecule, shell a), the
+// threads over shell b. Also the per-molecule maximum (non-negative doubles
+// order like their bit patterns, so an integer atomicMax works).
+__global__ void jk_dmax_kernel(const JkMol *__restrict__ mols, const int *__restrict__ sh_mol,
+                               const int *__restrict__ mol_sh0, const int *__restrict__ sh_ao,
+                               const int *__restrict__ sh_nc, int ndm, double *__restrict__ dmax,
+                               unsigned long long *__restrict__ dmax_mol)
+{
+    const int s = blockIdx.x;
+    const int m = sh_mol[s];
+    const JkMol mol = mols[m];
+    const int a = s - mol_sh0[m];
+    const int na = sh_nc[s], aoa = sh_ao[s];
+    const long long nn = (long long)mol.nao * mol.nao;
+    double rowmax = 0.0;
+    for (int b = threadIdx.x; b < mol.nsh; b += blockDim.x) {
+        const int sb = mol_sh0[m] + b;
+        const int nb = sh_nc[sb], aob = sh_ao[sb];
+        double mx = 0.0;
+        for (int k = 0; k < ndm; ++k)
+            for (int i = 0; i < na; ++i)
+                for (int j = 0; j < nb; ++j)
+                    mx = fmax(mx, fabs(mol.D[k * nn + (long long)(aoa + i) * mol.nao + aob + j]));
+        dmax[mol.dmax_off + (long long)a * mol.nsh + b] = mx;
+        rowmax = fmax(rowmax, mx);
+    }
+    for (int o = 16; o > 0; o >>= 1) rowmax = fmax(rowmax, __shfl_xor_sync(0xffffffffu, rowmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dmax_mol + m, (unsigned long long)__double_as_longlong(rowmax));
+}
+
+// In-place J <- X + X^T (and the same for K) per molecule and density, on
+// 32 x 32 tiles of the upper triangle. tile_off[m] is the first tile of
+// molecule m (prefix over nt(nt+1)/2, nt = ceil(nao/32)).
+__global__ void jk_symmetrize_kernel(const JkMol *__restrict__ mols, const long long *__restrict__ tile_off,
+                                     int nmol, int ndm, int do_j, int do_k)
+{
+    __shared__ double t1[32][33], t2[32][33];
+    const long long tile = blockIdx.x;
+    int lo = 0, hi = nmol - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (tile_off[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const int m = lo;
+    const JkMol mol = mols[m];
+    const int n = mol.nao;
+    const int nt = (n + 31) / 32;
+    long long r = tile - tile_off[m];
+    int ti = 0;
+    while (r >= nt - ti) { r -= nt - ti; ++ti; }
+    const int tj = ti + (int)r;
+    const int dm = blockIdx.y;
+    double *X = (blockIdx.z == 0) ? mol.J : mol.K;
+    if ((blockIdx.z == 0 && !do_j) || (blockIdx.z == 1 && !do_k) || X == nullptr) return;
+    X += (long long)dm * n * n;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        int i = ti * 32 + k, j = tj * 32 + tx;
+        t1[k][tx] = (i < n && j < n) ? X[(long long)i * n + j] : 0.0;
+        i = tj * 32 + k; j = ti * 32 + tx;
+        t2[k][tx] = (i < n && j < n) ? X[(long long)i * n + j] : 0.0;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        int i = ti * 32 + k, j = tj * 32 + tx;
+        if (i < n && j < n) X[(long long)i * n + j] = t1[k][tx] + t2[tx][k];
+        i = tj * 32 + k; j = ti * 32 + tx;
+        if (i < n && j < n && ti != tj) X[(long long)i * n + j] = t2[k][tx] + t1[tx][k];
+    }
+}
+
+// FMA-chain throughput probes: 8 independent chains per thread so that the
+// FMA pipe, not latency, bounds the loop. The result is stored only if it
+// equals a value it never takes, which keeps the loop alive.
+template <typename T>
+__global__ void jk_fma_probe_kernel(int iters, T seed, T *sink)
+{
+    T a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    const T m = (T)0.9999999, c = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            a0 = a0 * m + c; a1 = a1 * m + c; a2 = a2 * m + c; a3 = a3 * m + c;
+            a4 = a4 * m + c; a5 = a5 * m + c; a6 = a6 * m + c; a7 = a7 * m + c;
+        }
+    }
+    T r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (r == (T)-12345.678) sink[0] = r;
+}

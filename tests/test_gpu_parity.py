@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: max |dJ|, |dK| <= 1e-10 for all-FP64 builds and <= 1e-8 for
+mixed precision (the bounds the JK method is held to); the FP32-only mode is
+checked against a looser bound derived from single precision.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_09772_gb300 import jk, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL_MIXED = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    jk.load_library()
+
+
+def gpu_jk(mol, D=None, **kw):
+    eng = jk.JK(mol)
+    try:
+        for k, v in kw.pop("options", {}).items():
+            eng.set_option(k, v)
+        Dn = mol.D if D is None else D
+        Dt = torch.tensor(np.asarray(Dn), dtype=torch.float64, device="cuda")
+        J, K, st = eng.build(Dt, stats=True, **kw)
+        torch.cuda.synchronize()
+        return (None if J is None else J.cpu().numpy(), None if K is None else K.cpu().numpy(), st)
+    finally:
+        eng.close()
+
+
+def maxdiff(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max())
+
+
+def test_tiny_fp64_matches_oracle():
+    mol = synth.tiny_631gs()
+    J, K, st = gpu_jk(mol, cutoff=1e-13, precision="fp64")
+    Jr, Kr, nq = oracle.jk(mol, cutoff=1e-13)
+    assert maxdiff(J, Jr) <= TOL64
+    assert maxdiff(K, Kr) <= TOL64
+    assert abs(st["quartets_fp64"] - nq) <= 2
+    assert st["quartets_fp32"] == 0
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+def test_random_molecules_fp64(seed):
+    mol = synth.random_small_molecule(seed, natm=2 + seed % 2, lmax=2, max_nprim=3)
+    J, K, _ = gpu_jk(mol, cutoff=1e-13)
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    assert maxdiff(J, Jr) <= TOL64
+    assert maxdiff(K, Kr) <= TOL64
+
+
+def test_ten_atom_molecule_spans_many_ket_chunks():
+    mol = synth.batched_molecule(0, natm=10)
+    J, K, st = gpu_jk(mol, cutoff=1e-13)
+    Jr, Kr, nq = oracle.jk(mol, cutoff=1e-13)
+    assert maxdiff(J, Jr) <= TOL64
+    assert maxdiff(K, Kr) <= TOL64
+    assert abs(st["quartets_fp64"] - nq) <= max(2, nq // 100000)
+
+
+def test_two_densities():
+    mol = synth.tiny_631gs(n_dm=2)
+    J, K, _ = gpu_jk(mol, cutoff=1e-13)
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    assert J.shape == (2, mol.nao, mol.nao)
+    assert maxdiff(J, Jr) <= TOL64
+    assert maxdiff(K, Kr) <= TOL64
+
+
+@pytest.mark.parametrize("wj,wk", [(1, 0), (0, 1)])
+def test_j_only_and_k_only(wj, wk):
+    mol = synth.tiny_631gs()
+    J, K, _ = gpu_jk(mol, cutoff=1e-13, with_j=bool(wj), with_k=bool(wk))
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13, with_j=wj, with_k=wk)
+    if wj:
+        assert maxdiff(J, Jr) <= TOL64 and K is None
+    if wk:
+        assert maxdiff(K, Kr) <= TOL64 and J is None
+
+
+@pytest.mark.parametrize("cutoff", [0.0, 1e-10, 1e-6])
+def test_cutoffs(cutoff):
+    mol = synth.tiny_631gs()
+    J, K, st = gpu_jk(mol, cutoff=cutoff)
+    Jr, Kr, nq = oracle.jk(mol, cutoff=cutoff)
+    assert maxdiff(J, Jr) <= TOL64
+    assert maxdiff(K, Kr) <= TOL64
+    assert abs(st["quartets_fp64"] - nq) <= 2
+
+
+def test_schwarz_factors_match_oracle():
+    mol = synth.tiny_631gs()
+    eng = jk.JK(mol)
+    Q = jk.jk_schwarz(eng.h)
+    eng.close()
+    Qr = oracle.schwarz(mol)
+    assert np.allclose(Q, Qr, rtol=1e-12, atol=1e-300)
+
+
+def test_without_density_screening():
+    mol = synth.tiny_631gs()
+    J, K, _ = gpu_jk(mol, cutoff=1e-11, options={"use_dmax": 0})
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-11, use_dmax=False)
+    assert maxdiff(J, Jr) <= TOL64
+    assert maxdiff(K, Kr) <= TOL64
+
+
+def test_single_s_shell_and_single_d_shell():
+    rng = np.random.default_rng(0)
+    for lst in ([[(0, [1.3])]], [[(2, [0.8])]], [[(1, [2.0, 0.5])], [(0, [0.7])]]):
+        mol = synth.custom_basis_molecule(rng.uniform(0, 1.5, size=(len(lst), 3)), lst, rng, nocc=1)
+        J, K, _ = gpu_jk(mol, cutoff=0.0)
+        Jr, Kr, _ = oracle.jk(mol, cutoff=0.0)
+        assert maxdiff(J, Jr) <= TOL64 and maxdiff(K, Kr) <= TOL64
+
+
+def test_batch_matches_per_molecule_oracle():
+    mols = [synth.random_small_molecule(20 + i, natm=2, lmax=2, max_nprim=2) for i in range(3)]
+    mols.append(synth.tiny_631gs())
+    eng = jk.JK(mols)
+    Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
+    J, K, st = eng.build(Ds, cutoff=1e-13, stats=True)
+    torch.cuda.synchronize()
+    eng.close()
+    total = 0
+    for m, j, k in zip(mols, J, K):
+        Jr, Kr, nq = oracle.jk(m, cutoff=1e-13)
+        total += nq
+        assert maxdiff(j.cpu().numpy(), Jr) <= TOL64
+        assert maxdiff(k.cpu().numpy(), Kr) <= TOL64
+    assert abs(st["quartets_fp64"] - total) <= 4
+
+
+def test_repeated_builds_are_reproducible_to_atomic_reordering():
+    mol = synth.batched_molecule(1, natm=10)
+    eng = jk.JK(mol)
+    D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+    J1, K1, _ = eng.build(D)
+    J2, K2, _ = eng.build(D)
+    torch.cuda.synchronize()
+    eng.close()
+    assert float((J1 - J2).abs().max()) <= 1e-12
+    assert float((K1 - K2).abs().max()) <= 1e-12
+
+
+def test_mixed_precision_within_tolerance():
+    mol = synth.batched_molecule(2, natm=12)
+    J, K, st = gpu_jk(mol, cutoff=1e-13, precision="mixed")
+    Jr, Kr, nq = oracle.jk(mol, cutoff=1e-13)
+    assert st["quartets_fp32"] > 0 and st["quartets_fp64"] > 0
+    assert maxdiff(J, Jr) <= TOL_MIXED
+    assert maxdiff(K, Kr) <= TOL_MIXED
+
+
+def test_fp32_mode_error_is_single_precision_sized():
+    mol = synth.tiny_631gs()
+    J, K, st = gpu_jk(mol, cutoff=1e-13, precision="fp32")
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    assert st["quartets_fp64"] == 0
+    scale = max(np.abs(Jr).max(), 1.0)
+    assert maxdiff(J, Jr) <= 1e-4 * scale
+    assert maxdiff(K, Kr) <= 1e-4 * scale
+
+
+def test_bad_arguments_return_codes():
+    mol = synth.tiny_631gs()
+    eng = jk.JK(mol)
+    D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    lib = jk.load_library()
+    assert lib.jk_build(eng.h, D.data_ptr(), 0, 1, 1, 1e-13, 0, J.data_ptr(), K.data_ptr(), None, None) == jk.JK_ERR_ARG
+    assert lib.jk_build(eng.h, D.data_ptr(), 9, 1, 1, 1e-13, 0, J.data_ptr(), K.data_ptr(), None, None) == jk.JK_ERR_UNSUPPORTED
+    assert lib.jk_build(eng.h, D.data_ptr(), 1, 0, 0, 1e-13, 0, J.data_ptr(), K.data_ptr(), None, None) == jk.JK_ERR_ARG
+    assert lib.jk_build(eng.h, D.data_ptr(), 1, 1, 1, -1.0, 0, J.data_ptr(), K.data_ptr(), None, None) == jk.JK_ERR_ARG
+    assert lib.jk_build(eng.h, D.data_ptr(), 1, 1, 1, 1e-13, 7, J.data_ptr(), K.data_ptr(), None, None) == jk.JK_ERR_ARG
+    assert lib.jk_build(eng.h, None, 1, 1, 1, 1e-13, 0, J.data_ptr(), K.data_ptr(), None, None) == jk.JK_ERR_ARG
+    # the handle still works afterwards
+    J2, K2, _ = eng.build(D)
+    torch.cuda.synchronize()
+    eng.close()
+    Jr, Kr, _ = oracle.jk(mol)
+    assert maxdiff(J2.cpu().numpy(), Jr) <= TOL64
