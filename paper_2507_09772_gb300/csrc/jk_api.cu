@@ -119,12 +119,14 @@ struct KSpec {
     int nr() const { return (la + lb + lc + ld) / 2 + 1; }
     int ni() const { return (la + 1) * (lb + 1) * (lc + 1) * (ld + 1); }
     int smem_group_reals() const { return G() == 1 ? 0 : nr() * 3 * ni() + 2 * nr(); }
-    int block() const { return 128; }
+    // G <= 32: four warps, each holding 32/G groups; G > 32: one group per CTA
+    int block() const { return G() <= 32 ? 128 : ((G() + 31) / 32) * 32; }
     size_t smem_bytes() const
     {
-        int ngw = 32 / G();
-        return (size_t)4 * ngw * smem_group_reals() * (fp32 ? 4 : 8);
+        const size_t groups = G() <= 32 ? (size_t)4 * (32 / G()) : 1;
+        return groups * smem_group_reals() * (fp32 ? 4 : 8);
     }
+    int groups_per_cta() const { return G() <= 32 ? 4 * (32 / G()) : 1; }
 };
 
 struct KInfo {
@@ -377,6 +379,44 @@ int ensure_kernels(const std::vector<KSpec> &specs, std::vector<KInfo> &out)
     return JK_OK;
 }
 
+// ------------------------------------------------ real solid harmonics
+// Cartesian expansion of the unit-norm real solid harmonics S_lm, m = -l..l
+// (Helgaker, Jorgensen and Olsen, "Molecular Electronic-Structure Theory",
+// Eqs. 6.4.47-6.4.50; Schlegel and Frisch 1995). Row = Cartesian component
+// (x descending, then y), column = m + l. p shells keep (x, y, z). With the
+// normalisation N_lm each S_lm has the norm of z^l, i.e. of the (l,0,0)
+// component, so unit-norm inputs give unit-norm spherical functions.
+std::vector<double> solid_harmonics(int l)
+{
+    const int nc = ncart(l), ns = 2 * l + 1;
+    std::vector<double> C((size_t)nc * ns, 0.0);
+    if (l == 0) { C[0] = 1.0; return C; }
+    if (l == 1) { for (int i = 0; i < 3; ++i) C[i * 3 + i] = 1.0; return C; }
+    auto fact = [](int n) { double r = 1; for (int i = 2; i <= n; ++i) r *= i; return r; };
+    auto binom = [&](int n, int k) { return (k < 0 || k > n) ? 0.0 : fact(n) / (fact(k) * fact(n - k)); };
+    auto comp = [&](int lx, int ly) {
+        int idx = 0;
+        for (int x = l; x >= 0; --x)
+            for (int y = l - x; y >= 0; --y, ++idx)
+                if (x == lx && y == ly) return idx;
+        return -1;
+    };
+    for (int m = -l; m <= l; ++m) {
+        const int am = m < 0 ? -m : m;
+        const double N = std::sqrt(2.0 * fact(l + am) * fact(l - am) / (m == 0 ? 2.0 : 1.0)) / (std::ldexp(1.0, am) * fact(l));
+        const int vm2 = m < 0 ? 1 : 0;
+        for (int t = 0; t <= (l - am) / 2; ++t)
+            for (int u = 0; u <= t; ++u)
+                for (int k = vm2; k <= am; k += 2) {
+                    const int sgn = ((t + (k - vm2) / 2) & 1) ? -1 : 1;
+                    const double c = sgn * std::ldexp(1.0, -2 * t) * binom(l, t) * binom(l - t, am + t) * binom(t, u) * binom(am, k);
+                    const int lx = 2 * t + am - 2 * u - k, ly = 2 * u + k;
+                    C[(size_t)comp(lx, ly) * ns + (m + l)] += N * c;
+                }
+    }
+    return C;
+}
+
 // -------------------------------------------------------- fragment choice
 // Threads per quartet: G = ga*gb*gc*gd with each g dividing the Cartesian
 // size of its shell and G <= 32. G == 1 keeps the 2D tables in registers and
@@ -389,6 +429,7 @@ void choose_fragments(KSpec &s, bool symmetric)
     const int ne = nf[0] * nf[1] * nf[2] * nf[3];
     const int ni = s.ni();
     const int reg_cap = s.fp32 ? 96 : 48;     // per-thread fragment budget (reals)
+    const int gmax = symmetric ? 1024 : 256;  // threads per quartet (one CTA at most)
     const int g1_cap = s.fp32 ? 128 : 64;     // register-mode budget: fragment + 3 tables
     if (ne + 3 * ni <= g1_cap) { s.ga = s.gb = s.gc = s.gd = 1; return; }
     int best[4] = {1, 1, 1, 1};
@@ -400,12 +441,12 @@ void choose_fragments(KSpec &s, bool symmetric)
                 for (int d : divisors(nf[3])) {
                     if (symmetric && (a != c || b != d)) continue;
                     int g = a * b * c * d;
-                    if (g > 32 || g < 2) continue;
+                    if (g > gmax || g < 2) continue;
                     int ept = ne / g;
                     // prefer: fits the budget, then fewest threads, then fewest idle lanes
                     long fits = ept <= reg_cap ? 1 : 0;
-                    long idle = 32 % g;
-                    long score = fits * 1000000 + (fits ? (100 - g) * 1000 : (100000 - ept) * 10) - idle;
+                    long idle = g <= 32 ? 32 % g : (32 - g % 32) % 32;
+                    long score = fits * 100000000L + (fits ? (2000 - g) * 1000L : (1000000L - ept) * 10L) - idle;
                     if (score > best_score) { best_score = score; best[0] = a; best[1] = b; best[2] = c; best[3] = d; }
                 }
     s.ga = best[0]; s.gb = best[1]; s.gc = best[2]; s.gd = best[3];
@@ -441,6 +482,8 @@ struct Launch {
 };
 
 }  // namespace
+
+#define JK_MAX_BRANCHES 7
 
 struct jk_handle {
     int device = 0;
@@ -479,6 +522,22 @@ struct jk_handle {
     double init_ms = 0, compile_ms = 0;
     std::vector<cudaEvent_t> prof_ev;      // two per launch slot
     std::vector<jk_launch_prof> prof;
+    // spherical molecules: Cartesian scratch copies of D, J, K
+    std::vector<char> mol_sph;             // per molecule
+    std::vector<int> sh_ao_user;           // molecule-local AO offset in the caller's basis
+    int *d_sh_l = nullptr, *d_sh_sph = nullptr, *d_sh_aou = nullptr, *d_c2s_off = nullptr;
+    double *d_c2s = nullptr;
+    double *d_cart = nullptr;              // scratch: per spherical molecule 3 x ndm x nao_c^2
+    size_t cart_ndm = 0;
+    std::vector<size_t> cart_off;          // per molecule offset into d_cart
+    JkSphMol *d_sph = nullptr, *h_sph = nullptr;  // [0, nmol): to Cartesian, [nmol, 2 nmol): back
+    size_t cart_gen = 0;                   // bumps when the scratch moves (invalidates graphs)
+    // graphs and branch streams
+    int branches = 1;
+    cudaStream_t cap = nullptr;
+    cudaStream_t side[JK_MAX_BRANCHES] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[JK_MAX_BRANCHES] = {};
+    std::map<std::string, std::pair<cudaGraphExec_t, int>> graphs;
 };
 
 namespace {
@@ -496,6 +555,16 @@ void free_handle(jk_handle *h)
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (auto e : h->prof_ev) cudaEventDestroy(e);
+    cudaFree(h->d_sh_l); cudaFree(h->d_sh_sph); cudaFree(h->d_sh_aou); cudaFree(h->d_c2s_off);
+    cudaFree(h->d_c2s); cudaFree(h->d_cart); cudaFree(h->d_sph);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (int b = 0; b < JK_MAX_BRANCHES; ++b) {
+        if (h->side[b]) cudaStreamDestroy(h->side[b]);
+        if (h->ev_join[b]) cudaEventDestroy(h->ev_join[b]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->h_sph) cudaFreeHost(h->h_sph);
     delete h;
 }
 
@@ -531,7 +600,6 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
             return fail(JK_ERR_ARG, "shell %d has fields out of range", s);
         if (x.l > JK_LMAX) return fail(JK_ERR_UNSUPPORTED, "shell %d: l=%d above JK_LMAX=%d", s, x.l, JK_LMAX);
         if (x.nprim > JK_NPRIM_MAX) return fail(JK_ERR_UNSUPPORTED, "shell %d: nprim=%d above %d", s, x.nprim, JK_NPRIM_MAX);
-        if (x.spherical) return fail(JK_ERR_UNSUPPORTED, "spherical shells are not supported yet");
         for (int i = 0; i < x.nprim; ++i)
             if (!(exps[x.prim_off + i] > 0) || !std::isfinite(coeffs[x.prim_off + i]))
                 return fail(JK_ERR_ARG, "shell %d: non-positive exponent or non-finite coefficient", s);
@@ -550,18 +618,26 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     h->mol_sh0.assign(mol_shell_off, mol_shell_off + nmol + 1);
     h->sh_ao_cart.resize(nshell);
     std::vector<int> sh_mol(nshell), sh_nc(nshell);
+    h->sh_ao_user.resize(nshell);
     for (int m = 0; m < nmol; ++m) {
         int o = 0, ou = 0;
+        bool sph = false;
         for (int s = mol_shell_off[m]; s < mol_shell_off[m + 1]; ++s) {
             sh_mol[s] = m;
             h->sh_ao_cart[s] = o;
             sh_nc[s] = ncart(shells[s].l);
             o += ncart(shells[s].l);
-            ou = std::max(ou, shells[s].ao_off + ncart(shells[s].l));
+            if (shells[s].ao_off != ou)
+                return fail(JK_ERR_ARG, "shell %d: ao_off %d, expected %d (functions are laid out shell by shell)",
+                            s, shells[s].ao_off, ou);
+            h->sh_ao_user[s] = ou;
+            ou += shells[s].spherical ? 2 * shells[s].l + 1 : ncart(shells[s].l);
+            sph = sph || shells[s].spherical;
         }
         h->nao_cart.push_back(o);
-        h->nao_user.push_back(o);
-        (void)ou;
+        h->nao_user.push_back(ou);
+        h->mol_sph.push_back(sph ? 1 : 0);
+        h->spherical = h->spherical || sph;
     }
 
     // ---- shell types and pair classes
@@ -689,11 +765,12 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
             a.rys64 = h->d_rys64;
             a.Qout = d_q + ranges[k].first;
             a.npair = (int)(ranges[k].second - ranges[k].first);
-            const int ngw = 32 / specs[k].G();
-            long long warps = (a.npair + ngw - 1) / ngw;
-            unsigned grid = (unsigned)std::min<long long>((warps + 3) / 4, (long long)h->num_sms * 8);
+            const long long groups = specs[k].groups_per_cta();
+            unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((a.npair + groups - 1) / groups,
+                                                                                (long long)h->num_sms * 8));
             void *params[] = {&a};
-            CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, 128, 1, 1, (unsigned)ki[k].smem, 0, params, nullptr);
+            CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem, 0,
+                                            params, nullptr);
             if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "Schwarz launch failed: %d", (int)r);
         }
         CK(cudaDeviceSynchronize());
@@ -784,10 +861,32 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     CK(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 2 * nl));
     CK(cudaMalloc(&h->d_err, sizeof(int)));
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (h->spherical) {
+        std::vector<int> sl(nshell), ss(nshell), off(JK_LMAX + 2, 0);
+        for (int s2 = 0; s2 < nshell; ++s2) { sl[s2] = shells[s2].l; ss[s2] = shells[s2].spherical; }
+        std::vector<double> c2s;
+        for (int l = 0; l <= JK_LMAX; ++l) {
+            off[l] = (int)c2s.size();
+            auto C = solid_harmonics(l);
+            c2s.insert(c2s.end(), C.begin(), C.end());
+        }
+        if ((rc = upload(&h->d_sh_l, sl)) || (rc = upload(&h->d_sh_sph, ss)) ||
+            (rc = upload(&h->d_sh_aou, h->sh_ao_user)) || (rc = upload(&h->d_c2s_off, off)) ||
+            (rc = upload(&h->d_c2s, c2s)))
+            return rc;
+        CK(cudaMalloc(&h->d_sph, sizeof(JkSphMol) * 2 * nmol));
+        CK(cudaMallocHost(&h->h_sph, sizeof(JkSphMol) * 2 * nmol));
+    }
     CK(cudaMallocHost(&h->h_mols, sizeof(JkMol) * nmol));
     CK(cudaEventCreateWithFlags(&h->mol_copied, cudaEventDisableTiming));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
+    CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    for (int b = 0; b < JK_MAX_BRANCHES; ++b) {
+        CK(cudaStreamCreateWithFlags(&h->side[b], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
+    }
     CK(cudaDeviceSynchronize());
     h->init_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     *out = h.release();
@@ -837,35 +936,64 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
     if (rc) return rc;
     h->compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc).count();
 
+    // Cartesian scratch for spherical molecules (3 x ndm x nao_c^2 each)
+    if (h->spherical && h->cart_ndm < (size_t)ndm) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(h->d_cart);
+        h->d_cart = nullptr;
+        h->cart_off.assign(h->nmol, 0);
+        size_t tot = 0;
+        for (int m = 0; m < h->nmol; ++m)
+            if (h->mol_sph[m]) { h->cart_off[m] = tot; tot += 3 * (size_t)ndm * h->nao_cart[m] * h->nao_cart[m]; }
+        CK(cudaMalloc(&h->d_cart, sizeof(double) * std::max<size_t>(tot, 1)));
+        h->cart_ndm = ndm;
+        ++h->cart_gen;
+    }
     // per-molecule descriptors
     CK(cudaEventSynchronize(h->mol_copied));
     long long off = 0;
     for (int m = 0; m < h->nmol; ++m) {
         JkMol &x = h->h_mols[m];
-        x.D = D[m];
-        x.J = with_j ? J[m] : nullptr;
-        x.K = with_k ? K[m] : nullptr;
         x.nao = h->nao_cart[m];
+        if (h->mol_sph[m]) {
+            const size_t nn = (size_t)ndm * x.nao * x.nao;
+            double *base = h->d_cart + h->cart_off[m];
+            x.D = base;
+            x.J = with_j ? base + nn : nullptr;
+            x.K = with_k ? base + 2 * nn : nullptr;
+            JkSphMol &a = h->h_sph[m], &b = h->h_sph[h->nmol + m];
+            a.src[0] = D[m]; a.dst[0] = base; a.src[1] = nullptr; a.dst[1] = nullptr; a.nsrc = 1;
+            b.src[0] = x.J; b.dst[0] = with_j ? J[m] : nullptr;
+            b.src[1] = x.K; b.dst[1] = with_k ? K[m] : nullptr; b.nsrc = 2;
+            a.nao_c = b.nao_c = x.nao;
+            a.nao_s = b.nao_s = h->nao_user[m];
+            a.sh0 = b.sh0 = h->mol_sh0[m];
+            a.nsh = b.nsh = h->mol_sh0[m + 1] - h->mol_sh0[m];
+        } else {
+            x.D = D[m];
+            x.J = with_j ? J[m] : nullptr;
+            x.K = with_k ? K[m] : nullptr;
+            if (h->spherical) {
+                JkSphMol &a = h->h_sph[m], &b = h->h_sph[h->nmol + m];
+                a = JkSphMol{};
+                b = JkSphMol{};
+            }
+        }
         x.nsh = h->mol_sh0[m + 1] - h->mol_sh0[m];
         x.dmax_off = off;
         off += (long long)x.nsh * x.nsh;
     }
     if (stats) CK(cudaEventRecord(h->ev0, st));
     CK(cudaMemcpyAsync(h->d_mols, h->h_mols, sizeof(JkMol) * h->nmol, cudaMemcpyHostToDevice, st));
+    if (h->spherical)
+        CK(cudaMemcpyAsync(h->d_sph, h->h_sph, sizeof(JkSphMol) * 2 * h->nmol, cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(h->mol_copied, st));
+    int max_nsh = 0, max_nao = 0;
     for (int m = 0; m < h->nmol; ++m) {
-        size_t bytes = sizeof(double) * (size_t)ndm * h->nao_cart[m] * h->nao_cart[m];
-        if (with_j) CK(cudaMemsetAsync(J[m], 0, bytes, st));
-        if (with_k) CK(cudaMemsetAsync(K[m], 0, bytes, st));
+        max_nsh = std::max(max_nsh, h->mol_sh0[m + 1] - h->mol_sh0[m]);
+        max_nao = std::max(max_nao, h->nao_cart[m]);
     }
     const size_t nl = h->launches.size() * 2;
-    CK(cudaMemsetAsync(h->d_work, 0, sizeof(int) * nl, st));
-    CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 2 * nl, st));
-    CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, st));
-    jk_dmax_kernel<<<h->nshell, 128, 0, st>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
-                                              h->d_dmax, h->d_dmax_mol);
-    CK(cudaGetLastError());
-
     const double inf = INFINITY;
     const bool prof = h->profile && stats;
     if (prof && h->prof_ev.size() < 2 * specs.size()) {
@@ -873,52 +1001,132 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         h->prof_ev.resize(2 * specs.size());
         for (size_t e = have; e < h->prof_ev.size(); ++e) CK(cudaEventCreate(&h->prof_ev[e]));
     }
-    for (size_t k = 0; k < specs.size(); ++k) {
-        const Launch &L = h->launches[lidx[k]];
-        const PairClass &A = h->classes[L.c1], &B = h->classes[L.c2];
-        JkClassArgs a;
-        // bra and ket indices are relative to the base of their pair class
-        a.bra = h->d_pairs + A.off;
-        a.ket = h->d_pairs + B.off;
-        a.ket_beg = B.d_beg;
-        a.ket_end = B.d_end;
-        a.pp64 = h->d_pp64;
-        a.pp32 = h->d_pp32;
-        a.mols = h->d_mols;
-        a.dmax = h->d_dmax;
-        a.dmax_mol = reinterpret_cast<const double *>(h->d_dmax_mol);
-        a.rys64 = h->d_rys64;
-        a.rys32 = h->d_rys32;
-        const int slot = lidx[k] * 2 + tier[k];
-        a.work = h->d_work + slot;
-        a.stats = h->d_stats + 2 * slot;
-        a.err = h->d_err;
-        if (mode == JK_PREC_MIXED) {
-            const double t = std::max(cutoff, h->tau32);
-            if (tier[k] == 0) { a.lo = t; a.hi = inf; }
-            else { a.lo = cutoff; a.hi = t; }
-        } else {
-            a.lo = cutoff; a.hi = inf;
+    const int nbranch = prof ? 1 : std::max(1, std::min(h->branches, JK_MAX_BRANCHES + 1));
+    int nlaunch_aux = 0;
+
+    // Everything a build does on the device, in order, on stream s (and, for
+    // nbranch > 1, forked onto the handle's side streams and joined back).
+    auto enqueue = [&](cudaStream_t s0) -> int {
+        nlaunch_aux = 0;
+        if (h->spherical) {
+            dim3 g((unsigned)(((long long)max_nsh * max_nsh + 127) / 128), ndm, h->nmol);
+            jk_sph_kernel<<<g, 128, 0, s0>>>(h->d_sph, h->d_sh_l, h->d_sh_sph, h->d_sh_ao, h->d_sh_aou, h->d_c2s,
+                                             h->d_c2s_off, ndm, 1);
+            CK(cudaGetLastError());
+            ++nlaunch_aux;
         }
-        a.nbra = A.n;
-        a.same_class = (L.c1 == L.c2) ? 1 : 0;
-        a.with_j = with_j ? 1 : 0;
-        a.with_k = with_k ? 1 : 0;
-        a.use_dmax = h->use_dmax;
-        a.ndm = ndm;
-        int grid = std::max(1, ki[k].blocks_per_sm) * h->num_sms;
-        long long need = ((long long)A.n + 3) / 4;
-        if (need < grid) grid = (int)std::max(1LL, need);
-        void *params[] = {&a};
-        if (prof) CK(cudaEventRecord(h->prof_ev[2 * k], st));
-        CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, 128, 1, 1, (unsigned)ki[k].smem, (CUstream)st, params, nullptr);
-        if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "launch of %s failed: %d", specs[k].name().c_str(), (int)r);
-        if (prof) CK(cudaEventRecord(h->prof_ev[2 * k + 1], st));
-    }
-    if (h->ntiles > 0) {
-        dim3 grid((unsigned)h->ntiles, ndm, 2);
-        jk_symmetrize_kernel<<<grid, dim3(32, 8), 0, st>>>(h->d_mols, h->d_tile_off, h->nmol, ndm, with_j, with_k);
+        {
+            long long per = (long long)ndm * max_nao * max_nao;
+            dim3 g((unsigned)std::min<long long>((per + 255) / 256, 4096), h->nmol);
+            jk_zero_kernel<<<g, 256, 0, s0>>>(h->d_mols, ndm);
+            CK(cudaGetLastError());
+            ++nlaunch_aux;
+        }
+        CK(cudaMemsetAsync(h->d_work, 0, sizeof(int) * nl, s0));
+        CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 2 * nl, s0));
+        CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, s0));
+        jk_dmax_kernel<<<h->nshell, 128, 0, s0>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
+                                                  h->d_dmax, h->d_dmax_mol);
         CK(cudaGetLastError());
+        ++nlaunch_aux;
+        if (nbranch > 1) {
+            CK(cudaEventRecord(h->ev_fork, s0));
+            for (int b = 1; b < nbranch; ++b) CK(cudaStreamWaitEvent(h->side[b - 1], h->ev_fork, 0));
+        }
+        for (size_t k = 0; k < specs.size(); ++k) {
+            cudaStream_t sk = (nbranch > 1 && k % nbranch) ? h->side[k % nbranch - 1] : s0;
+            const Launch &L = h->launches[lidx[k]];
+            const PairClass &A = h->classes[L.c1], &B = h->classes[L.c2];
+            JkClassArgs a;
+            // bra and ket indices are relative to the base of their pair class
+            a.bra = h->d_pairs + A.off;
+            a.ket = h->d_pairs + B.off;
+            a.ket_beg = B.d_beg;
+            a.ket_end = B.d_end;
+            a.pp64 = h->d_pp64;
+            a.pp32 = h->d_pp32;
+            a.mols = h->d_mols;
+            a.dmax = h->d_dmax;
+            a.dmax_mol = reinterpret_cast<const double *>(h->d_dmax_mol);
+            a.rys64 = h->d_rys64;
+            a.rys32 = h->d_rys32;
+            const int slot = lidx[k] * 2 + tier[k];
+            a.work = h->d_work + slot;
+            a.stats = h->d_stats + 2 * slot;
+            a.err = h->d_err;
+            if (mode == JK_PREC_MIXED) {
+                const double t = std::max(cutoff, h->tau32);
+                if (tier[k] == 0) { a.lo = t; a.hi = inf; }
+                else { a.lo = cutoff; a.hi = t; }
+            } else {
+                a.lo = cutoff; a.hi = inf;
+            }
+            a.nbra = A.n;
+            a.same_class = (L.c1 == L.c2) ? 1 : 0;
+            a.with_j = with_j ? 1 : 0;
+            a.with_k = with_k ? 1 : 0;
+            a.use_dmax = h->use_dmax;
+            a.ndm = ndm;
+            int grid = std::max(1, ki[k].blocks_per_sm) * h->num_sms;
+            const long long units = specs[k].G() <= 32 ? 4 : 1;   // bra pairs in flight per CTA
+            long long need = ((long long)A.n + units - 1) / units;
+            if (need < grid) grid = (int)std::max(1LL, need);
+            void *params[] = {&a};
+            if (prof) CK(cudaEventRecord(h->prof_ev[2 * k], sk));
+            CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem,
+                                            (CUstream)sk, params, nullptr);
+            if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "launch of %s failed: %d", specs[k].name().c_str(), (int)r);
+            if (prof) CK(cudaEventRecord(h->prof_ev[2 * k + 1], sk));
+        }
+        if (nbranch > 1) {
+            for (int b = 1; b < nbranch; ++b) {
+                CK(cudaEventRecord(h->ev_join[b - 1], h->side[b - 1]));
+                CK(cudaStreamWaitEvent(s0, h->ev_join[b - 1], 0));
+            }
+        }
+        if (h->ntiles > 0) {
+            dim3 grid((unsigned)h->ntiles, ndm, 2);
+            jk_symmetrize_kernel<<<grid, dim3(32, 8), 0, s0>>>(h->d_mols, h->d_tile_off, h->nmol, ndm, with_j, with_k);
+            CK(cudaGetLastError());
+            ++nlaunch_aux;
+        }
+        if (h->spherical) {
+            dim3 g((unsigned)(((long long)max_nsh * max_nsh + 127) / 128), ndm, h->nmol);
+            jk_sph_kernel<<<g, 128, 0, s0>>>(h->d_sph + h->nmol, h->d_sh_l, h->d_sh_sph, h->d_sh_ao, h->d_sh_aou,
+                                             h->d_c2s, h->d_c2s_off, ndm, 0);
+            CK(cudaGetLastError());
+            ++nlaunch_aux;
+        }
+        return JK_OK;
+    };
+
+    if (h->use_graph && !prof) {
+        // one CUDA graph per flag combination, captured on the handle's own
+        // stream and replayed on the caller's; per-call pointers live in the
+        // device descriptors copied above, so the graph stays valid.
+        char keyb[160];
+        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%d/%d/%zu", ndm, with_j, with_k, mode, cutoff, h->tau32,
+                 h->use_dmax, nbranch, h->cart_gen);
+        std::string key = keyb;
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            int erc = enqueue(h->cap);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
+            if (erc) { if (graph) cudaGraphDestroy(graph); return erc; }
+            if (ce != cudaSuccess) return fail(JK_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(JK_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+            it = h->graphs.emplace(key, std::make_pair(exec, nlaunch_aux)).first;
+        }
+        nlaunch_aux = it->second.second;
+        CK(cudaGraphLaunch(it->second.first, st));
+    } else {
+        int erc = enqueue(st);
+        if (erc) return erc;
     }
     if (stats) {
         CK(cudaEventRecord(h->ev1, st));
@@ -931,7 +1139,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         memset(stats, 0, sizeof(*stats));
         stats->ms = ms;
-        stats->kernel_launches = (int64_t)specs.size() + 1 + (h->ntiles > 0 ? 1 : 0);
+        stats->kernel_launches = (int64_t)specs.size() + 1 + nlaunch_aux;
         if (prof) h->prof.clear();
         for (size_t k = 0; k < specs.size(); ++k) {
             const int slot = lidx[k] * 2 + tier[k];
@@ -1029,6 +1237,10 @@ int jk_set_option(jk_handle *h, const char *key, double value)
     else if (k == "use_graph") h->use_graph = value != 0;
     else if (k == "use_dmax") h->use_dmax = value != 0;
     else if (k == "profile") h->profile = value != 0;
+    else if (k == "branches") {
+        if (!(value >= 1 && value <= JK_MAX_BRANCHES + 1)) return fail(JK_ERR_ARG, "branches must be in [1, %d]", JK_MAX_BRANCHES + 1);
+        h->branches = (int)value;
+    }
     else return fail(JK_ERR_ARG, "unknown option '%s'", key);
     return JK_OK;
 }
@@ -1043,6 +1255,8 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "use_graph") *value = h->use_graph;
     else if (k == "use_dmax") *value = h->use_dmax;
     else if (k == "profile") *value = h->profile;
+    else if (k == "branches") *value = h->branches;
+    else if (k == "graphs") *value = (double)h->graphs.size();
     else if (k == "init_ms") *value = h->init_ms;
     else if (k == "compile_ms") *value = h->compile_ms;
     else if (k == "npairs") *value = (double)h->h_pairs.size();

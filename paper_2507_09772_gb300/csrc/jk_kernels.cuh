@@ -175,7 +175,7 @@ struct JkShape {
     // reals of shared memory per group (G > 1): 2D tables and the roots
     static constexpr int SMEM_GROUP = (G == 1) ? 0 : (NR * 3 * NI + 2 * NR);
     static_assert(NFA % GA == 0 && NFB % GB == 0 && NFC % GC == 0 && NFD % GD == 0, "fragment");
-    static_assert(G <= 32, "groups are warp-local");
+    static_assert(G <= 1024, "a group fits one CTA");
 };
 
 // Offsets into a 2D table for the components a thread owns (G > 1).
@@ -226,6 +226,15 @@ __device__ __forceinline__ void jk_make_offsets(int ga, int gb, int gc, int gd,
     }
 }
 
+// Barrier of one group: a warp-local group syncs its lanes, a group of more
+// than 32 threads is the whole CTA.
+template <int G>
+__device__ __forceinline__ void jk_group_sync(unsigned gmask)
+{
+    if constexpr (G <= 32) __syncwarp(gmask);
+    else __syncthreads();
+}
+
 // ------------------------------------------------ one contracted quartet
 // Accumulates the thread's fragment T[EPT] of the contracted block (ab|cd)
 // over every primitive quartet (eq:rys0). `grp` is the group's shared
@@ -234,7 +243,7 @@ template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
           int GA, int GB, int GC, int GD, typename R>
 __device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
                                            const typename JkPP<R>::T *__restrict__ pp,
-                                           const R *__restrict__ rys, R *grp, unsigned gmask, int tg,
+                                           const R *__restrict__ rys, R *grp, unsigned gmask, int tg, bool act,
                                            const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD>> &off,
                                            R (&T)[JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::EPT])
 {
@@ -291,13 +300,13 @@ __device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
                 }
             } else {
                 R *roots = grp + NR * 3 * S::NI;   // [0, NR): u ; [NR, 2NR): w * pref
-                if (tg < NR) {
+                for (int r = tg; r < NR; r += S::G) {
                     R u, w;
-                    jk_rys_one<NR>(Tt, tg, rys, u, w);
-                    roots[tg] = u;
-                    roots[NR + tg] = w * pref;
+                    jk_rys_one<NR>(Tt, r, rys, u, w);
+                    roots[r] = u;
+                    roots[NR + r] = w * pref;
                 }
-                __syncwarp(gmask);
+                jk_group_sync<S::G>(gmask);
                 for (int task = tg; task < 3 * NR; task += S::G) {
                     const int r = task / 3, dir = task - 3 * r;
                     const R u = roots[r];
@@ -312,7 +321,8 @@ __device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
                     jk_build_2d<LA, LB, LC, LD, R>(pa - uq * pqd, qc + up * pqd, b10, b01, b00, i00, abd, cdd,
                                                    grp + (r * 3 + dir) * S::NI);
                 }
-                __syncwarp(gmask);
+                jk_group_sync<S::G>(gmask);
+                if (act) {
 #pragma unroll
                 for (int ia = 0; ia < S::FA; ++ia)
 #pragma unroll
@@ -332,7 +342,8 @@ __device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
                                            grp[(r * 3 + 2) * S::NI + oz];
                                 T[k] += acc;
                             }
-                __syncwarp(gmask);
+                }
+                jk_group_sync<S::G>(gmask);
             }
         }
     }
@@ -345,219 +356,317 @@ template <typename R> __device__ __forceinline__ const R *jk_rys(const JkClassAr
 template <> __device__ __forceinline__ const double *jk_rys<double>(const JkClassArgs &a) { return a.rys64; }
 template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassArgs &a) { return a.rys32; }
 
+// ------------------------------------------------- screening of a candidate
+// Keep (bra, ket j) iff lo < Q_ab Q_cd Dmax <= hi; `stop` when even the
+// molecule's largest density element cannot lift this ket (and every later
+// one, kets being sorted by Q) above lo.
+__device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
+                                          const double *dmx, double dmol, int j, int ke, bool &sig, bool &stop)
+{
+    sig = false;
+    stop = false;
+    if (j >= ke) return;
+    const double bq = bra.Q * args.ket[j].Q;
+    if (bq * dmol <= args.lo) { stop = true; return; }
+    double dm = 1.0;
+    if (args.use_dmax) {
+        const int c = args.ket[j].a_loc, d = args.ket[j].b_loc;
+        const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
+        dm = 0.0;
+        if (args.with_j) dm = fmax(__ldg(dmx + a * ns + b), __ldg(dmx + c * ns + d));
+        if (args.with_k) {
+            dm = fmax(dm, fmax(__ldg(dmx + a * ns + c), __ldg(dmx + a * ns + d)));
+            dm = fmax(dm, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
+        }
+    }
+    const double B = bq * dm;
+    sig = (B > args.lo) && (B <= args.hi);
+}
+
+// ------------------------------------------ contraction with the density
+// The thread's fragment T of (ab|cd), degeneracy f: J_ab partial kept in
+// jab (flushed once per bra pair), the other five blocks by FP64 atomics.
+template <int FA, int FB, int FC, int FD, int NDM, int DOJ, int DOK, typename R>
+__device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f, const JkMol &mol,
+                                            int a0, int b0, int c0, int d0, R (&jab)[NDM][FA][FB])
+{
+    const long long nn = (long long)mol.nao * mol.nao;
+    const int nao = mol.nao;
+#pragma unroll
+    for (int m = 0; m < NDM; ++m) {
+        const double *D = mol.D + m * nn;
+        if (DOJ) {
+            R Dcd[FC][FD], Dab[FA][FB];
+#pragma unroll
+            for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                for (int id = 0; id < FD; ++id) Dcd[ic][id] = (R)__ldg(D + (long long)(c0 + ic) * nao + d0 + id);
+#pragma unroll
+            for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                for (int ib = 0; ib < FB; ++ib) Dab[ia][ib] = (R)__ldg(D + (long long)(a0 + ia) * nao + b0 + ib);
+            R jcd[FC][FD];
+#pragma unroll
+            for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                for (int id = 0; id < FD; ++id) jcd[ic][id] = (R)0;
+#pragma unroll
+            for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                for (int ib = 0; ib < FB; ++ib) {
+                    R sum = (R)0;
+#pragma unroll
+                    for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                        for (int id = 0; id < FD; ++id) {
+                            const R t = T[((ia * FB + ib) * FC + ic) * FD + id];
+                            sum += t * Dcd[ic][id];
+                            jcd[ic][id] += t * Dab[ia][ib];
+                        }
+                    jab[m][ia][ib] += (R)2 * f * sum;
+                }
+#pragma unroll
+            for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                for (int id = 0; id < FD; ++id)
+                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, (double)((R)2 * f * jcd[ic][id]));
+        }
+        if (DOK) {
+            R Dbd[FB][FD], Dbc[FB][FC], Dad[FA][FD], Dac[FA][FC];
+#pragma unroll
+            for (int ib = 0; ib < FB; ++ib) {
+#pragma unroll
+                for (int id = 0; id < FD; ++id) Dbd[ib][id] = (R)__ldg(D + (long long)(b0 + ib) * nao + d0 + id);
+#pragma unroll
+                for (int ic = 0; ic < FC; ++ic) Dbc[ib][ic] = (R)__ldg(D + (long long)(b0 + ib) * nao + c0 + ic);
+            }
+#pragma unroll
+            for (int ia = 0; ia < FA; ++ia) {
+#pragma unroll
+                for (int id = 0; id < FD; ++id) Dad[ia][id] = (R)__ldg(D + (long long)(a0 + ia) * nao + d0 + id);
+#pragma unroll
+                for (int ic = 0; ic < FC; ++ic) Dac[ia][ic] = (R)__ldg(D + (long long)(a0 + ia) * nao + c0 + ic);
+            }
+            R kac[FA][FC], kad[FA][FD], kbc[FB][FC], kbd[FB][FD];
+#pragma unroll
+            for (int ia = 0; ia < FA; ++ia) {
+#pragma unroll
+                for (int ic = 0; ic < FC; ++ic) kac[ia][ic] = (R)0;
+#pragma unroll
+                for (int id = 0; id < FD; ++id) kad[ia][id] = (R)0;
+            }
+#pragma unroll
+            for (int ib = 0; ib < FB; ++ib) {
+#pragma unroll
+                for (int ic = 0; ic < FC; ++ic) kbc[ib][ic] = (R)0;
+#pragma unroll
+                for (int id = 0; id < FD; ++id) kbd[ib][id] = (R)0;
+            }
+#pragma unroll
+            for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                for (int ib = 0; ib < FB; ++ib)
+#pragma unroll
+                    for (int ic = 0; ic < FC; ++ic)
+#pragma unroll
+                        for (int id = 0; id < FD; ++id) {
+                            const R t = T[((ia * FB + ib) * FC + ic) * FD + id];
+                            kac[ia][ic] += t * Dbd[ib][id];
+                            kad[ia][id] += t * Dbc[ib][ic];
+                            kbc[ib][ic] += t * Dad[ia][id];
+                            kbd[ib][id] += t * Dac[ia][ic];
+                        }
+            double *K = mol.K + m * nn;
+#pragma unroll
+            for (int ia = 0; ia < FA; ++ia) {
+#pragma unroll
+                for (int ic = 0; ic < FC; ++ic)
+                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, (double)(f * kac[ia][ic]));
+#pragma unroll
+                for (int id = 0; id < FD; ++id)
+                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, (double)(f * kad[ia][id]));
+            }
+#pragma unroll
+            for (int ib = 0; ib < FB; ++ib) {
+#pragma unroll
+                for (int ic = 0; ic < FC; ++ic)
+                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, (double)(f * kbc[ib][ic]));
+#pragma unroll
+                for (int id = 0; id < FD; ++id)
+                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, (double)(f * kbd[ib][id]));
+            }
+        }
+    }
+}
+
+template <int FA, int FB, int NDM, typename R>
+__device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol &mol, int a0, int b0)
+{
+    const long long nn = (long long)mol.nao * mol.nao;
+#pragma unroll
+    for (int m = 0; m < NDM; ++m)
+#pragma unroll
+        for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+            for (int ib = 0; ib < FB; ++ib)
+                if (jab[m][ia][ib] != (R)0)
+                    atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, (double)jab[m][ia][ib]);
+}
+
 // ------------------------------------------------------- the class kernel
+// Persistent: warps (or, for groups of more than 32 threads, whole CTAs)
+// take bra pairs from a global counter until none are left.
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
           int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R>
-__global__ void __launch_bounds__(128) jk_class_kernel(const JkClassArgs args)
+__global__ void __launch_bounds__(JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G <= 32 ? 128
+                                  : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G + 31) / 32) * 32)
+jk_class_kernel(const JkClassArgs args)
 {
     typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
-    constexpr int G = S::G, NGW = 32 / G;
+    constexpr int G = S::G;
     constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
     extern __shared__ double jk_smem_raw[];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int gw = lane / G, tg = lane - gw * G;
-    const bool active = gw < NGW;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gw * G));
-    R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
-    // fragment coordinates of this thread inside its group
-    const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
-    JkOffsets<S> off;
-    jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
     const typename JkPP<R>::T *pp = jk_pp<R>(args);
     const R *rys = jk_rys<R>(args);
 
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(args.work, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= args.nbra) break;
-        const JkPair bra = args.bra[item];
-        const JkMol mol = args.mols[bra.mol];
-        const int kb = args.same_class ? item : args.ket_beg[bra.mol];
-        const int ke = args.ket_end[bra.mol];
-        const double *dmx = args.dmax + mol.dmax_off;
-        const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
-        const long long nn = (long long)mol.nao * mol.nao;
-        const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
-        R jab[NDM][FA][FB];
+    if constexpr (G <= 32) {
+        constexpr int NGW = 32 / G;
+        const int wib = threadIdx.x >> 5;
+        const int gw = lane / G, tg = lane - gw * G;
+        const bool active = gw < NGW;
+        const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((active ? gw : 0) * G));
+        R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
+        const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
+        JkOffsets<S> off;
+        jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        for (;;) {
+            int item = 0;
+            if (lane == 0) item = atomicAdd(args.work, 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item >= args.nbra) break;
+            const JkPair bra = args.bra[item];
+            const JkMol mol = args.mols[bra.mol];
+            const int kb = args.same_class ? item : args.ket_beg[bra.mol];
+            const int ke = args.ket_end[bra.mol];
+            const double *dmx = args.dmax + mol.dmax_off;
+            const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
+            const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+            R jab[NDM][FA][FB];
 #pragma unroll
-        for (int m = 0; m < NDM; ++m)
+            for (int m = 0; m < NDM; ++m)
 #pragma unroll
-            for (int i = 0; i < FA; ++i)
+                for (int i = 0; i < FA; ++i)
 #pragma unroll
-                for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
-        unsigned long long nq = 0;
-
-        for (int base = kb; base < ke; base += 32) {
-            const int j = base + lane;
-            bool sig = false, stop = false;
-            if (j < ke) {
-                const double bq = bra.Q * args.ket[j].Q;
-                if (bq * dmol <= args.lo) {
-                    stop = true;
-                } else {
-                    double dm = 1.0;
-                    if (args.use_dmax) {
-                        const int c = args.ket[j].a_loc, d = args.ket[j].b_loc;
-                        const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
-                        dm = 0.0;
-                        if (args.with_j) dm = fmax(__ldg(dmx + a * ns + b), __ldg(dmx + c * ns + d));
-                        if (args.with_k) {
-                            dm = fmax(dm, fmax(__ldg(dmx + a * ns + c), __ldg(dmx + a * ns + d)));
-                            dm = fmax(dm, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
-                        }
+                    for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
+            unsigned long long nq = 0;
+            for (int base = kb; base < ke; base += 32) {
+                bool sig, stop;
+                jk_screen(args, bra, mol, dmx, dmol, base + lane, ke, sig, stop);
+                unsigned mask = __ballot_sync(0xffffffffu, sig);
+                nq += __popc(mask);
+                while (mask) {
+                    int myket = -1;
+                    if (active) {
+                        unsigned mm = mask;
+                        for (int q = 0; q < gw && mm; ++q) mm &= mm - 1;
+                        if (mm) myket = base + __ffs(mm) - 1;
                     }
-                    const double B = bq * dm;
-                    sig = (B > args.lo) && (B <= args.hi);
-                }
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, sig);
-            nq += __popc(mask);
-            while (mask) {
-                int myket = -1;
-                if (active) {
-                    unsigned m = mask;
-                    for (int s = 0; s < gw && m; ++s) m &= m - 1;
-                    if (m) myket = base + __ffs(m) - 1;
-                }
 #pragma unroll 1
-                for (int s = 0; s < NGW && mask; ++s) mask &= mask - 1;
-                if (myket >= 0) {
+                    for (int q = 0; q < NGW && mask; ++q) mask &= mask - 1;
+                    if (myket >= 0) {
+                        const JkPair ket = args.ket[myket];
+                        R T[S::EPT];
+#pragma unroll
+                        for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
+                        jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(bra, ket, pp, rys, grp, gmask, tg, true, off, T);
+                        R f = (R)1;
+                        if (bra.a == bra.b) f *= (R)0.5;
+                        if (ket.a == ket.b) f *= (R)0.5;
+                        if (args.same_class && myket == item) f *= (R)0.5;
+                        jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
+                                                                     ket.b_ao + gd * FD, jab);
+                    }
+                    __syncwarp();
+                }
+                if (__any_sync(0xffffffffu, stop)) break;
+            }
+            if (DOJ && active) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+            if (lane == 0 && nq) {
+                atomicAdd(args.stats, nq);
+                atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+            }
+        }
+    } else {
+        // one group per CTA of round_up(G, 32) threads
+        __shared__ int s_item;
+        __shared__ unsigned s_mask;
+        __shared__ int s_stop;
+        const int tg = threadIdx.x;
+        const bool act = tg < G;
+        const int tgc = act ? tg : 0;
+        const int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
+        R *grp = reinterpret_cast<R *>(jk_smem_raw);
+        JkOffsets<S> off;
+        jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        for (;;) {
+            if (threadIdx.x == 0) s_item = atomicAdd(args.work, 1);
+            __syncthreads();
+            const int item = s_item;
+            __syncthreads();
+            if (item >= args.nbra) break;
+            const JkPair bra = args.bra[item];
+            const JkMol mol = args.mols[bra.mol];
+            const int kb = args.same_class ? item : args.ket_beg[bra.mol];
+            const int ke = args.ket_end[bra.mol];
+            const double *dmx = args.dmax + mol.dmax_off;
+            const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
+            const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+            R jab[NDM][FA][FB];
+#pragma unroll
+            for (int m = 0; m < NDM; ++m)
+#pragma unroll
+                for (int i = 0; i < FA; ++i)
+#pragma unroll
+                    for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
+            unsigned long long nq = 0;
+            for (int base = kb; base < ke; base += 32) {
+                if (threadIdx.x < 32) {
+                    bool sig, stop;
+                    jk_screen(args, bra, mol, dmx, dmol, base + lane, ke, sig, stop);
+                    const unsigned msk = __ballot_sync(0xffffffffu, sig);
+                    const int anystop = __any_sync(0xffffffffu, stop);
+                    if (lane == 0) { s_mask = msk; s_stop = anystop; }
+                }
+                __syncthreads();
+                unsigned mask = s_mask;
+                const int stop = s_stop;
+                __syncthreads();
+                nq += __popc(mask);
+                while (mask) {
+                    const int myket = base + __ffs(mask) - 1;
+                    mask &= mask - 1;
                     const JkPair ket = args.ket[myket];
                     R T[S::EPT];
 #pragma unroll
                     for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
-                    jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(bra, ket, pp, rys, grp, gmask, tg, off, T);
-                    R f = (R)1;
-                    if (bra.a == bra.b) f *= (R)0.5;
-                    if (ket.a == ket.b) f *= (R)0.5;
-                    if (args.same_class && myket == item) f *= (R)0.5;
-                    const int c0 = ket.a_ao + gc * FC, d0 = ket.b_ao + gd * FD;
-#pragma unroll
-                    for (int m = 0; m < NDM; ++m) {
-                        const double *D = mol.D + m * nn;
-                        const int nao = mol.nao;
-                        if (DOJ) {
-                            R Dcd[FC][FD], Dab[FA][FB];
-#pragma unroll
-                            for (int ic = 0; ic < FC; ++ic)
-#pragma unroll
-                                for (int id = 0; id < FD; ++id) Dcd[ic][id] = (R)__ldg(D + (long long)(c0 + ic) * nao + d0 + id);
-#pragma unroll
-                            for (int ia = 0; ia < FA; ++ia)
-#pragma unroll
-                                for (int ib = 0; ib < FB; ++ib) Dab[ia][ib] = (R)__ldg(D + (long long)(a0 + ia) * nao + b0 + ib);
-                            R jcd[FC][FD];
-#pragma unroll
-                            for (int ic = 0; ic < FC; ++ic)
-#pragma unroll
-                                for (int id = 0; id < FD; ++id) jcd[ic][id] = (R)0;
-#pragma unroll
-                            for (int ia = 0; ia < FA; ++ia)
-#pragma unroll
-                                for (int ib = 0; ib < FB; ++ib) {
-                                    R s = (R)0;
-#pragma unroll
-                                    for (int ic = 0; ic < FC; ++ic)
-#pragma unroll
-                                        for (int id = 0; id < FD; ++id) {
-                                            const R t = T[((ia * FB + ib) * FC + ic) * FD + id];
-                                            s += t * Dcd[ic][id];
-                                            jcd[ic][id] += t * Dab[ia][ib];
-                                        }
-                                    jab[m][ia][ib] += (R)2 * f * s;
-                                }
-#pragma unroll
-                            for (int ic = 0; ic < FC; ++ic)
-#pragma unroll
-                                for (int id = 0; id < FD; ++id)
-                                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, (double)((R)2 * f * jcd[ic][id]));
-                        }
-                        if (DOK) {
-                            R Dbd[FB][FD], Dbc[FB][FC], Dad[FA][FD], Dac[FA][FC];
-#pragma unroll
-                            for (int ib = 0; ib < FB; ++ib) {
-#pragma unroll
-                                for (int id = 0; id < FD; ++id) Dbd[ib][id] = (R)__ldg(D + (long long)(b0 + ib) * nao + d0 + id);
-#pragma unroll
-                                for (int ic = 0; ic < FC; ++ic) Dbc[ib][ic] = (R)__ldg(D + (long long)(b0 + ib) * nao + c0 + ic);
-                            }
-#pragma unroll
-                            for (int ia = 0; ia < FA; ++ia) {
-#pragma unroll
-                                for (int id = 0; id < FD; ++id) Dad[ia][id] = (R)__ldg(D + (long long)(a0 + ia) * nao + d0 + id);
-#pragma unroll
-                                for (int ic = 0; ic < FC; ++ic) Dac[ia][ic] = (R)__ldg(D + (long long)(a0 + ia) * nao + c0 + ic);
-                            }
-                            R kac[FA][FC], kad[FA][FD], kbc[FB][FC], kbd[FB][FD];
-#pragma unroll
-                            for (int ia = 0; ia < FA; ++ia) {
-#pragma unroll
-                                for (int ic = 0; ic < FC; ++ic) kac[ia][ic] = (R)0;
-#pragma unroll
-                                for (int id = 0; id < FD; ++id) kad[ia][id] = (R)0;
-                            }
-#pragma unroll
-                            for (int ib = 0; ib < FB; ++ib) {
-#pragma unroll
-                                for (int ic = 0; ic < FC; ++ic) kbc[ib][ic] = (R)0;
-#pragma unroll
-                                for (int id = 0; id < FD; ++id) kbd[ib][id] = (R)0;
-                            }
-#pragma unroll
-                            for (int ia = 0; ia < FA; ++ia)
-#pragma unroll
-                                for (int ib = 0; ib < FB; ++ib)
-#pragma unroll
-                                    for (int ic = 0; ic < FC; ++ic)
-#pragma unroll
-                                        for (int id = 0; id < FD; ++id) {
-                                            const R t = T[((ia * FB + ib) * FC + ic) * FD + id];
-                                            kac[ia][ic] += t * Dbd[ib][id];
-                                            kad[ia][id] += t * Dbc[ib][ic];
-                                            kbc[ib][ic] += t * Dad[ia][id];
-                                            kbd[ib][id] += t * Dac[ia][ic];
-                                        }
-                            double *K = mol.K + m * nn;
-#pragma unroll
-                            for (int ia = 0; ia < FA; ++ia) {
-#pragma unroll
-                                for (int ic = 0; ic < FC; ++ic)
-                                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, (double)(f * kac[ia][ic]));
-#pragma unroll
-                                for (int id = 0; id < FD; ++id)
-                                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, (double)(f * kad[ia][id]));
-                            }
-#pragma unroll
-                            for (int ib = 0; ib < FB; ++ib) {
-#pragma unroll
-                                for (int ic = 0; ic < FC; ++ic)
-                                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, (double)(f * kbc[ib][ic]));
-#pragma unroll
-                                for (int id = 0; id < FD; ++id)
-                                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, (double)(f * kbd[ib][id]));
-                            }
-                        }
+                    jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(bra, ket, pp, rys, grp, 0u, tg, act, off, T);
+                    if (act) {
+                        R f = (R)1;
+                        if (bra.a == bra.b) f *= (R)0.5;
+                        if (ket.a == ket.b) f *= (R)0.5;
+                        if (args.same_class && myket == item) f *= (R)0.5;
+                        jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
+                                                                     ket.b_ao + gd * FD, jab);
                     }
                 }
-                __syncwarp();
+                if (stop) break;
             }
-            if (__any_sync(0xffffffffu, stop)) break;
-        }
-        if (DOJ && active) {
-#pragma unroll
-            for (int m = 0; m < NDM; ++m)
-#pragma unroll
-                for (int ia = 0; ia < FA; ++ia)
-#pragma unroll
-                    for (int ib = 0; ib < FB; ++ib)
-                        if (jab[m][ia][ib] != (R)0)
-                            atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, (double)jab[m][ia][ib]);
-        }
-        if (lane == 0 && nq) {
-            atomicAdd(args.stats, nq);
-            atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+            if (DOJ && act) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+            if (threadIdx.x == 0 && nq) {
+                atomicAdd(args.stats, nq);
+                atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+            }
         }
     }
 }
@@ -566,46 +675,83 @@ __global__ void __launch_bounds__(128) jk_class_kernel(const JkClassArgs args)
 // Diagonal quartets (ab|ab) of one pair class in FP64; Q_ab is the square
 // root of the largest |(mu nu|mu nu)| (eq:schwartz at shell level).
 template <int LA, int LB, int NPA, int NPB, int GA, int GB, int GC, int GD>
-__global__ void __launch_bounds__(128) jk_schwarz_kernel(const JkSchwarzArgs args)
+__global__ void __launch_bounds__(JkShape<LA, LB, LA, LB, GA, GB, GC, GD>::G <= 32 ? 128
+                                  : ((JkShape<LA, LB, LA, LB, GA, GB, GC, GD>::G + 31) / 32) * 32)
+jk_schwarz_kernel(const JkSchwarzArgs args)
 {
     typedef JkShape<LA, LB, LA, LB, GA, GB, GC, GD> S;
     static_assert(GA == GC && GB == GD, "diagonal elements must stay inside one thread");
-    constexpr int G = S::G, NGW = 32 / G;
+    constexpr int G = S::G;
     constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
     extern __shared__ double jk_smem_raw[];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int gw = lane / G, tg = lane - gw * G;
-    const bool active = gw < NGW;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gw * G));
-    double *grp = jk_smem_raw + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
-    const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
-    JkOffsets<S> off;
-    jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD>(ga, gb, gc, gd, off);
-    const int warps_total = (gridDim.x * blockDim.x) >> 5;
-    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int base = gwarp * NGW; base < args.npair; base += warps_total * NGW) {
-        const int pi = base + gw;
-        const bool mine = active && pi < args.npair;
-        double mx = 0.0;
-        if (mine) {
+    if constexpr (G <= 32) {
+        constexpr int NGW = 32 / G;
+        const int wib = threadIdx.x >> 5;
+        const int gw = lane / G, tg = lane - gw * G;
+        const bool active = gw < NGW;
+        const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((active ? gw : 0) * G));
+        double *grp = jk_smem_raw + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
+        const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
+        JkOffsets<S> off;
+        jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        const int warps_total = (gridDim.x * blockDim.x) >> 5;
+        const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        for (int base = gwarp * NGW; base < args.npair; base += warps_total * NGW) {
+            const int pi = base + gw;
+            const bool mine = active && pi < args.npair;
+            double mx = 0.0;
+            if (mine) {
+                const JkPair pr = args.pairs[pi];
+                double T[S::EPT];
+#pragma unroll
+                for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
+                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
+                if (ga == gc && gb == gd) {
+#pragma unroll
+                    for (int ia = 0; ia < FA; ++ia)
+#pragma unroll
+                        for (int ib = 0; ib < FB; ++ib)
+                            mx = fmax(mx, fabs(T[((ia * FB + ib) * FC + ia) * FD + ib]));
+                }
+            }
+            double gmx = mx;
+            for (int q = 0; q < G; ++q) gmx = fmax(gmx, __shfl_sync(0xffffffffu, mx, (gw * G + q) & 31));
+            if (mine && tg == 0) args.Qout[pi] = sqrt(gmx);
+            __syncwarp();
+        }
+    } else {
+        __shared__ double s_max[32];
+        const int tg = threadIdx.x;
+        const bool act = tg < G;
+        const int tgc = act ? tg : 0;
+        const int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
+        double *grp = jk_smem_raw;
+        JkOffsets<S> off;
+        jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        for (int pi = blockIdx.x; pi < args.npair; pi += gridDim.x) {
             const JkPair pr = args.pairs[pi];
             double T[S::EPT];
 #pragma unroll
             for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, args.pp64, args.rys64, grp, gmask, tg, off, T);
-            if (ga == gc && gb == gd) {
+            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
+            double mx = 0.0;
+            if (act && ga == gc && gb == gd) {
 #pragma unroll
                 for (int ia = 0; ia < FA; ++ia)
 #pragma unroll
                     for (int ib = 0; ib < FB; ++ib)
                         mx = fmax(mx, fabs(T[((ia * FB + ib) * FC + ia) * FD + ib]));
             }
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_max[threadIdx.x >> 5] = mx;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double m2 = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, s_max[w]);
+                args.Qout[pi] = sqrt(m2);
+            }
+            __syncthreads();
         }
-        // group max through the group's lanes
-        double gmx = mx;
-        for (int s = 0; s < G; ++s) gmx = fmax(gmx, __shfl_sync(0xffffffffu, mx, (gw * G + s) & 31));
-        if (mine && tg == 0) args.Qout[pi] = sqrt(gmx);
-        __syncwarp();
     }
 }

@@ -135,3 +135,88 @@ __global__ void jk_fma_probe_kernel(int iters, T seed, T *sink)
     T r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
     if (r == (T)-12345.678) sink[0] = r;
 }
+
+// Zero the J/K accumulators of every molecule (pointers read from the
+// device descriptors, so a captured graph stays valid when they change).
+__global__ void jk_zero_kernel(const JkMol *__restrict__ mols, int ndm)
+{
+    const JkMol mol = mols[blockIdx.y];
+    const long long n = (long long)ndm * mol.nao * mol.nao;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (mol.J) mol.J[i] = 0.0;
+        if (mol.K) mol.K[i] = 0.0;
+    }
+}
+
+// Spherical <-> Cartesian transforms, one thread per (shell a, shell b)
+// block of one molecule and density. c2s holds, per l, the ncart(l) x (2l+1)
+// coefficients (row-major) at c2s_off[l]; a Cartesian shell uses the
+// identity. Directions:
+//   to_cart = 1: Xc[a][b] = C_a Xs[a][b] C_b^T   (density, spherical -> Cartesian)
+//   to_cart = 0: Xs[a][b] = C_a^T Xc[a][b] C_b   (J and K, Cartesian -> spherical)
+struct JkSphMol {
+    const double *src[2];   // up to two matrices per call (J and K, or D)
+    double *dst[2];
+    int nsrc;
+    int nao_c, nao_s;
+    int sh0, nsh;           // global index of the first shell, shell count
+};
+
+__global__ void jk_sph_kernel(const JkSphMol *__restrict__ mols, const int *__restrict__ sh_l,
+                              const int *__restrict__ sh_sph, const int *__restrict__ sh_aoc,
+                              const int *__restrict__ sh_aos, const double *__restrict__ c2s,
+                              const int *__restrict__ c2s_off, int ndm, int to_cart)
+{
+    const JkSphMol M = mols[blockIdx.z];
+    const long long nblk = (long long)M.nsh * M.nsh;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nblk) return;
+    const int a = M.sh0 + (int)(t / M.nsh), b = M.sh0 + (int)(t % M.nsh);
+    const int la = sh_l[a], lb = sh_l[b];
+    const int nca = (la + 1) * (la + 2) / 2, ncb = (lb + 1) * (lb + 2) / 2;
+    const int nsa = sh_sph[a] ? 2 * la + 1 : nca, nsb = sh_sph[b] ? 2 * lb + 1 : ncb;
+    const double *Ca = c2s + c2s_off[la], *Cb = c2s + c2s_off[lb];
+    const int dm = blockIdx.y;
+    for (int w = 0; w < M.nsrc; ++w) {
+        const double *S = M.src[w];
+        double *Dst = M.dst[w];
+        if (!S || !Dst) continue;
+        if (to_cart) {
+            S += (long long)dm * M.nao_s * M.nao_s;
+            Dst += (long long)dm * M.nao_c * M.nao_c;
+            for (int i = 0; i < nca; ++i)
+                for (int j = 0; j < ncb; ++j) {
+                    double s = 0.0;
+                    for (int m = 0; m < nsa; ++m) {
+                        const double ca = sh_sph[a] ? Ca[i * nsa + m] : (double)(i == m);
+                        if (ca == 0.0) continue;
+                        double r = 0.0;
+                        for (int n = 0; n < nsb; ++n) {
+                            const double cb = sh_sph[b] ? Cb[j * nsb + n] : (double)(j == n);
+                            r += cb * S[(long long)(sh_aos[a] + m) * M.nao_s + sh_aos[b] + n];
+                        }
+                        s += ca * r;
+                    }
+                    Dst[(long long)(sh_aoc[a] + i) * M.nao_c + sh_aoc[b] + j] = s;
+                }
+        } else {
+            S += (long long)dm * M.nao_c * M.nao_c;
+            Dst += (long long)dm * M.nao_s * M.nao_s;
+            for (int m = 0; m < nsa; ++m)
+                for (int n = 0; n < nsb; ++n) {
+                    double s = 0.0;
+                    for (int i = 0; i < nca; ++i) {
+                        const double ca = sh_sph[a] ? Ca[i * nsa + m] : (double)(i == m);
+                        if (ca == 0.0) continue;
+                        double r = 0.0;
+                        for (int j = 0; j < ncb; ++j) {
+                            const double cb = sh_sph[b] ? Cb[j * nsb + n] : (double)(j == n);
+                            r += cb * S[(long long)(sh_aoc[a] + i) * M.nao_c + sh_aoc[b] + j];
+                        }
+                        s += ca * r;
+                    }
+                    Dst[(long long)(sh_aos[a] + m) * M.nao_s + sh_aos[b] + n] = s;
+                }
+        }
+    }
+}
