@@ -96,6 +96,38 @@ typedef struct {
     double flops_model;                      /* modelled FLOPs of those quartets */
 } jk_launch_prof;
 
+/* Learned precision router (the MIXED_ROUTED mode): a 12 -> 64 -> 64 -> 1
+ * MLP, BF16 weights in use, FP32 accumulation. It predicts, for a quartet in
+ * the band tau32 < B <= K tau32 (B = Q_ab Q_cd Dmax), y = log10(max|T| / (Q_ab
+ * Q_cd)), and the quartet runs in FP32 iff log10(B / tau32) + y + margin <= 0.
+ * theta is the FP32 master copy, flat: W1[16][64] b1[64] W2[64][64] b2[64]
+ * W3[64] b3 (inputs padded to 16, rows 12..15 unused). The features are
+ * normalised as (x - mu) * isd. */
+#define JK_ROUTER_NIN 12
+#define JK_ROUTER_NPARAM 5313
+#define JK_ROUTER_MAGIC 0x4a4b5254u
+typedef struct {
+    uint32_t magic;     /* JK_ROUTER_MAGIC */
+    uint32_t version;   /* 1 */
+    float mu[16], isd[16];
+    float theta[JK_ROUTER_NPARAM];
+    float margin;       /* added to the prediction before the routing test */
+    float quantile;     /* the pinball-loss quantile it was trained with */
+} jk_router_blob;
+
+typedef struct {
+    int32_t steps;      /* optimiser steps */
+    int32_t batch;      /* samples per step */
+    float lr;           /* Adam learning rate */
+    float quantile;     /* pinball-loss quantile in (0, 1) */
+    uint64_t seed;      /* initialisation and sampling */
+} jk_train_opts;
+
+typedef struct {
+    double loss_first, loss_last;  /* mean pinball loss of the first / last 50 steps */
+    double ms;                     /* wall time of the training */
+} jk_train_stats;
+
 typedef struct jk_handle jk_handle;
 
 /* One molecule. shells: nshell records (host); coords: natm x 3 (host,
@@ -152,6 +184,32 @@ int jk_schwarz(jk_handle *h, double *Q_host);
 
 int jk_destroy(jk_handle *h);
 
+/* Router training data from a full FP64 build (which it also returns in J,
+ * K): for every quartet the build evaluates inside the band (tau32, K tau32]
+ * it writes the 12 features to X[i*12..] and the label y = log10(max|T| /
+ * (Q_ab Q_cd)) to y[i] (X, y: device, capacity cap); *n receives the number
+ * of band quartets seen (only the first cap are written). Synchronises. */
+int jk_router_collect(jk_handle *h, const double *const *D, int32_t n_dm, double cutoff, double *const *J,
+                      double *const *K, float *X, float *y, int64_t cap, int64_t *n, void *stream);
+
+/* Train the router on the device with the library's own forward/backward
+ * kernels (Adam, pinball loss). X: n x 12, y: n (device). Writes the result
+ * to *out (host). Feature normalisation is computed from X. */
+int jk_router_train(const float *X, const float *y, int64_t n, const jk_train_opts *opts, jk_router_blob *out,
+                    jk_train_stats *stats);
+
+/* Predictions (margin included) for n feature rows (device in and out). */
+int jk_router_forward(const jk_router_blob *w, const float *X, int64_t n, float *y_out);
+
+/* Mean pinball loss over the n rows and its gradient with respect to theta
+ * (host array of JK_ROUTER_NPARAM), from the training kernel's backward
+ * pass. X, y: device. */
+int jk_router_gradient(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
+                       float *grad_host, double *loss);
+
+/* Install router weights on a handle (enables JK_PREC_MIXED_ROUTED). */
+int jk_router_load(jk_handle *h, const jk_router_blob *w);
+
 /* After a build with option "profile" = 1 and non-NULL stats: copies up to
  * `max` launch records into out and their count into *n. */
 int jk_profile(jk_handle *h, jk_launch_prof *out, int32_t max, int32_t *n);
@@ -161,12 +219,13 @@ int jk_profile(jk_handle *h, jk_launch_prof *out, int32_t max, int32_t *n);
 int jk_measure_peak(int32_t which, double ms, double *flops_per_s);
 
 /* Ahead-of-time compilation of one class kernel (angular momenta la..ld,
- * primitive counts na..nd, n_dm, flags, fp32 = 1 for the FP32 tier) into
+ * primitive counts na..nd, n_dm, flags, fp32 = 1 for the FP32 tier, mode 0
+ * plain / 1 routed / 2 router-label logging) into
  * the on-disk kernel cache (JK_KERNEL_CACHE, else next to the library).
  * Needs no GPU. *threads_per_quartet receives the fragmentation chosen.
  * JK_ERR_COMPILE with the NVRTC log in jk_last_error() on failure. */
 int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na, int32_t nb, int32_t nc,
-                     int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32,
+                     int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32, int32_t mode,
                      int32_t *threads_per_quartet, double *compile_ms);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -11,6 +11,7 @@
 #include "jk.h"
 #include "jk_types.h"
 #include "jk_util.cuh"
+#include "jk_train.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -104,6 +105,7 @@ struct KSpec {
     int la = 0, lb = 0, lc = 0, ld = 0, na = 1, nb = 1, nc = 1, nd = 1;
     int ga = 1, gb = 1, gc = 1, gd = 1;
     int ndm = 1, doj = 1, dok = 1, fp32 = 0;
+    int mode = 0;  // 0 plain, 1 routed (learned router in the band), 2 label logging
 
     std::string name() const
     {
@@ -111,8 +113,8 @@ struct KSpec {
         if (kind == 1)
             snprintf(b, sizeof b, "jk_schwarz_kernel<%d,%d,%d,%d,%d,%d,%d,%d>", la, lb, na, nb, ga, gb, gc, gd);
         else
-            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s>", la, lb, lc,
-                     ld, na, nb, nc, nd, ga, gb, gc, gd, ndm, doj, dok, fp32 ? "float" : "double");
+            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s,%d>", la, lb, lc,
+                     ld, na, nb, nc, nd, ga, gb, gc, gd, ndm, doj, dok, fp32 ? "float" : "double", mode);
         return b;
     }
     int G() const { return ga * gb * gc * gd; }
@@ -166,9 +168,11 @@ std::string cache_dir()
 
 std::vector<std::string> nvrtc_options(const KSpec &s)
 {
-    std::vector<std::string> o = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
-    if (s.fp32) o.push_back("--use_fast_math");
-    return o;
+    // No --use_fast_math for the FP32 tier: the pair data already hold every
+    // exponential, and identical compile options in both tiers keep the
+    // router's decisions bit-identical across the FP64 and FP32 kernels.
+    (void)s;
+    return {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
 }
 
 uint64_t spec_key(const KSpec &s)
@@ -532,6 +536,11 @@ struct jk_handle {
     std::vector<size_t> cart_off;          // per molecule offset into d_cart
     JkSphMol *d_sph = nullptr, *h_sph = nullptr;  // [0, nmol): to Cartesian, [nmol, 2 nmol): back
     size_t cart_gen = 0;                   // bumps when the scratch moves (invalidates graphs)
+    // learned router
+    JkPairFeat *d_pfeat = nullptr;         // aligned with d_pairs
+    JkRouterDev *d_router = nullptr;
+    bool has_router = false;
+    unsigned long long *d_logn = nullptr;
     // graphs and branch streams
     int branches = 1;
     cudaStream_t cap = nullptr;
@@ -557,6 +566,7 @@ void free_handle(jk_handle *h)
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     cudaFree(h->d_sh_l); cudaFree(h->d_sh_sph); cudaFree(h->d_sh_aou); cudaFree(h->d_c2s_off);
     cudaFree(h->d_c2s); cudaFree(h->d_cart); cudaFree(h->d_sph);
+    cudaFree(h->d_pfeat); cudaFree(h->d_router); cudaFree(h->d_logn);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
     if (h->cap) cudaStreamDestroy(h->cap);
     for (int b = 0; b < JK_MAX_BRANCHES; ++b) {
@@ -812,6 +822,38 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
         k0 = k1;
     }
     if ((rc = upload(&h->d_pairs, h->h_pairs))) return rc;
+    {
+        // router features per pair: exponent-sum range, |A-B|, log10 Q, centre
+        // of the most diffuse primitive pair, l_a + l_b
+        std::vector<JkPairFeat> pf(h->h_pairs.size());
+        for (size_t k = 0; k < pf.size(); ++k) {
+            const JkPair &pr = h->h_pairs[k];
+            const jk_shell &sa = shells[pr.a], &sb = shells[pr.b];
+            const double *A = coords + 3 * sa.atom, *B = coords + 3 * sb.atom;
+            double pmin = 1e300, pmax = 0, pcx = 0, pcy = 0, pcz = 0;
+            for (int i = 0; i < sa.nprim; ++i)
+                for (int j = 0; j < sb.nprim; ++j) {
+                    const double al = exps[sa.prim_off + i], be = exps[sb.prim_off + j], p = al + be;
+                    pmax = std::max(pmax, p);
+                    if (p < pmin) {
+                        pmin = p;
+                        pcx = (al * A[0] + be * B[0]) / p;
+                        pcy = (al * A[1] + be * B[1]) / p;
+                        pcz = (al * A[2] + be * B[2]) / p;
+                    }
+                }
+            JkPairFeat &f = pf[k];
+            f.lpmin = (float)std::log(pmin);
+            f.lpmax = (float)std::log(pmax);
+            f.rab = (float)std::sqrt(pr.ABx * pr.ABx + pr.ABy * pr.ABy + pr.ABz * pr.ABz);
+            f.lq = (float)std::log10(pr.Q);
+            f.pcx = (float)pcx; f.pcy = (float)pcy; f.pcz = (float)pcz;
+            f.lsum = (float)(sa.l + sb.l);
+        }
+        if ((rc = upload(&h->d_pfeat, pf))) return rc;
+        CK(cudaMalloc(&h->d_router, sizeof(JkRouterDev)));
+        CK(cudaMalloc(&h->d_logn, sizeof(unsigned long long)));
+    }
     for (auto &c : h->classes) {
         if ((rc = upload(&c.d_beg, c.beg)) || (rc = upload(&c.d_end, c.end))) return rc;
     }
@@ -858,7 +900,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     CK(cudaMalloc(&h->d_mols, sizeof(JkMol) * nmol));
     const size_t nl = h->launches.size() * 2;
     CK(cudaMalloc(&h->d_work, sizeof(int) * nl));
-    CK(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 2 * nl));
+    CK(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 3 * nl));
     CK(cudaMalloc(&h->d_err, sizeof(int)));
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
     if (h->spherical) {
@@ -893,8 +935,14 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     return JK_OK;
 }
 
+struct LogSpec {
+    float *x, *y;
+    long long cap;
+};
+
 int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int with_k, double cutoff,
-               int mode, double *const *J, double *const *K, void *stream, jk_stats *stats)
+               int mode, double *const *J, double *const *K, void *stream, jk_stats *stats,
+               const LogSpec *logs = nullptr)
 {
     if (!h) return fail(JK_ERR_ARG, "handle is NULL");
     if (!D) return fail(JK_ERR_ARG, "D is NULL");
@@ -903,7 +951,9 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
     if (!with_j && !with_k) return fail(JK_ERR_ARG, "with_j and with_k are both 0");
     if (!(cutoff >= 0) || !std::isfinite(cutoff)) return fail(JK_ERR_ARG, "cutoff must be finite and >= 0");
     if (mode < JK_PREC_FP64 || mode > JK_PREC_FP32) return fail(JK_ERR_ARG, "bad precision_mode %d", mode);
-    if (mode == JK_PREC_MIXED_ROUTED) return fail(JK_ERR_UNSUPPORTED, "router not loaded");
+    if (mode == JK_PREC_MIXED_ROUTED && !h->has_router)
+        return fail(JK_ERR_ARG, "MIXED_ROUTED needs router weights (jk_router_load)");
+    if (logs && mode != JK_PREC_FP64) return fail(JK_ERR_ARG, "label logging runs in FP64");
     if (with_j && !J) return fail(JK_ERR_ARG, "J is NULL with with_j");
     if (with_k && !K) return fail(JK_ERR_ARG, "K is NULL with with_k");
     for (int m = 0; m < h->nmol; ++m) {
@@ -921,10 +971,12 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
     std::vector<int> lidx, tier;
     for (size_t i = 0; i < h->launches.size(); ++i) {
         for (int t = 0; t < 2; ++t) {
-            bool use = (t == 0) ? (mode == JK_PREC_FP64 || mode == JK_PREC_MIXED) : (mode == JK_PREC_FP32 || mode == JK_PREC_MIXED);
+            const bool two = mode == JK_PREC_MIXED || mode == JK_PREC_MIXED_ROUTED;
+            bool use = (t == 0) ? (mode == JK_PREC_FP64 || two) : (mode == JK_PREC_FP32 || two);
             if (!use) continue;
             KSpec s = h->launches[i].spec[t];
             s.ndm = ndm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0;
+            s.mode = logs ? 2 : (mode == JK_PREC_MIXED_ROUTED ? 1 : 0);
             specs.push_back(s);
             lidx.push_back((int)i);
             tier.push_back(t);
@@ -1023,7 +1075,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             ++nlaunch_aux;
         }
         CK(cudaMemsetAsync(h->d_work, 0, sizeof(int) * nl, s0));
-        CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 2 * nl, s0));
+        CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 3 * nl, s0));
         CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, s0));
         jk_dmax_kernel<<<h->nshell, 128, 0, s0>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
                                                   h->d_dmax, h->d_dmax_mol);
@@ -1052,15 +1104,29 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.rys32 = h->d_rys32;
             const int slot = lidx[k] * 2 + tier[k];
             a.work = h->d_work + slot;
-            a.stats = h->d_stats + 2 * slot;
+            a.stats = h->d_stats + 3 * slot;
             a.err = h->d_err;
+            const double tau = std::max(cutoff, h->tau32);
+            const double band_hi = tau * h->router_band;
             if (mode == JK_PREC_MIXED) {
-                const double t = std::max(cutoff, h->tau32);
-                if (tier[k] == 0) { a.lo = t; a.hi = inf; }
-                else { a.lo = cutoff; a.hi = t; }
+                if (tier[k] == 0) { a.lo = tau; a.hi = inf; }
+                else { a.lo = cutoff; a.hi = tau; }
+            } else if (mode == JK_PREC_MIXED_ROUTED) {
+                if (tier[k] == 0) { a.lo = tau; a.hi = inf; }
+                else { a.lo = cutoff; a.hi = band_hi; }
             } else {
                 a.lo = cutoff; a.hi = inf;
             }
+            a.bra_feat = h->d_pfeat + A.off;
+            a.ket_feat = h->d_pfeat + B.off;
+            a.router = h->d_router;
+            a.tau = tau;
+            a.band_hi = band_hi;
+            a.tier = tier[k];
+            a.log_x = logs ? logs->x : nullptr;
+            a.log_y = logs ? logs->y : nullptr;
+            a.log_n = h->d_logn;
+            a.log_cap = logs ? logs->cap : 0;
             a.nbra = A.n;
             a.same_class = (L.c1 == L.c2) ? 1 : 0;
             a.with_j = with_j ? 1 : 0;
@@ -1100,7 +1166,8 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         return JK_OK;
     };
 
-    if (h->use_graph && !prof) {
+    if (logs) CK(cudaMemsetAsync(h->d_logn, 0, sizeof(unsigned long long), st));
+    if (h->use_graph && !prof && !logs) {
         // one CUDA graph per flag combination, captured on the handle's own
         // stream and replayed on the caller's; per-call pointers live in the
         // device descriptors copied above, so the graph stays valid.
@@ -1133,19 +1200,21 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         CK(cudaStreamSynchronize(st));
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-        std::vector<unsigned long long> cnt(2 * nl);
-        CK(cudaMemcpy(cnt.data(), h->d_stats, sizeof(unsigned long long) * 2 * nl, cudaMemcpyDeviceToHost));
+        std::vector<unsigned long long> cnt(3 * nl);
+        CK(cudaMemcpy(cnt.data(), h->d_stats, sizeof(unsigned long long) * 3 * nl, cudaMemcpyDeviceToHost));
         int err = 0;
         CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         memset(stats, 0, sizeof(*stats));
+        int64_t routed_fp32 = 0;
         stats->ms = ms;
-        stats->kernel_launches = (int64_t)specs.size() + 1 + nlaunch_aux;
+        stats->kernel_launches = (int64_t)specs.size() + nlaunch_aux;
         if (prof) h->prof.clear();
         for (size_t k = 0; k < specs.size(); ++k) {
             const int slot = lidx[k] * 2 + tier[k];
-            unsigned long long nq = cnt[2 * slot], np = cnt[2 * slot + 1];
+            unsigned long long nq = cnt[3 * slot], np = cnt[3 * slot + 1];
             if (tier[k] == 0) stats->quartets_fp64 += (int64_t)nq;
             else stats->quartets_fp32 += (int64_t)nq;
+            if (tier[k] == 1 && mode == JK_PREC_MIXED_ROUTED) routed_fp32 += (int64_t)cnt[3 * slot + 2];
             stats->prim_quartets += (int64_t)np;
             stats->flops_model += (double)nq * class_flops(specs[k], ndm);
             if (prof) {
@@ -1166,11 +1235,35 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                 h->prof.push_back(p);
             }
         }
+        stats->quartets_routed = routed_fp32;
         if (err) {
             CK(cudaMemset(h->d_err, 0, sizeof(int)));
             return fail(err == JK_ERR_DEV_TIMEOUT ? JK_ERR_TIMEOUT : JK_ERR_CUDA, "device error word %d", err);
         }
     }
+    return JK_OK;
+}
+
+// Device weights for inference from the FP32 master copy (BF16 rounding).
+void router_dev_from_blob(const jk_router_blob &w, JkRouterDev &d)
+{
+    memset(&d, 0, sizeof d);
+    for (int i = 0; i < 16; ++i) { d.mu[i] = w.mu[i]; d.isd[i] = w.isd[i]; }
+    for (int i = 0; i < JK_RT_NINP * JK_RT_NH; ++i) d.W1[i] = jk_f2bf(w.theta[JK_RT_OFF_W1 + i]);
+    for (int i = 0; i < JK_RT_NH; ++i) d.b1[i] = w.theta[JK_RT_OFF_B1 + i];
+    for (int i = 0; i < JK_RT_NH * JK_RT_NH; ++i) d.W2[i] = jk_f2bf(w.theta[JK_RT_OFF_W2 + i]);
+    for (int i = 0; i < JK_RT_NH; ++i) d.b2[i] = w.theta[JK_RT_OFF_B2 + i];
+    for (int i = 0; i < JK_RT_NH; ++i) d.W3[i] = jk_f2bf(w.theta[JK_RT_OFF_W3 + i]);
+    d.b3 = w.theta[JK_RT_OFF_B3];
+    d.margin = w.margin;
+}
+
+int check_blob(const jk_router_blob *w)
+{
+    if (!w) return fail(JK_ERR_ARG, "router weights are NULL");
+    if (w->magic != JK_ROUTER_MAGIC || w->version != 1) return fail(JK_ERR_ARG, "not a router weight blob");
+    for (int i = 0; i < JK_ROUTER_NPARAM; ++i)
+        if (!std::isfinite(w->theta[i])) return fail(JK_ERR_NAN, "non-finite router weight %d", i);
     return JK_OK;
 }
 
@@ -1294,6 +1387,185 @@ int jk_destroy(jk_handle *h)
     return JK_OK;
 }
 
+int jk_router_load(jk_handle *h, const jk_router_blob *w)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    int rc = check_blob(w);
+    if (rc) return rc;
+    JkRouterDev d;
+    router_dev_from_blob(*w, d);
+    CK(cudaMemcpy(h->d_router, &d, sizeof d, cudaMemcpyHostToDevice));
+    h->has_router = true;
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
+    h->graphs.clear();
+    return JK_OK;
+}
+
+int jk_router_collect(jk_handle *h, const double *const *D, int32_t n_dm, double cutoff, double *const *J,
+                      double *const *K, float *X, float *y, int64_t cap, int64_t *n, void *stream)
+{
+    if (!h || !X || !y || !n || cap < 1 || !J || !K) return fail(JK_ERR_ARG, "NULL argument or cap < 1");
+    LogSpec ls{X, y, (long long)cap};
+    jk_stats st;
+    int rc;
+    try {
+        rc = build_impl(h, D, n_dm, 1, 1, cutoff, JK_PREC_FP64, J, K, stream, &st, &ls);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_OOM, "host exception: %s", e.what());
+    }
+    if (rc) return rc;
+    unsigned long long cnt = 0;
+    CK(cudaMemcpy(&cnt, h->d_logn, sizeof cnt, cudaMemcpyDeviceToHost));
+    *n = (int64_t)cnt;
+    return JK_OK;
+}
+
+int jk_router_forward(const jk_router_blob *w, const float *X, int64_t n, float *y_out)
+{
+    int rc = check_blob(w);
+    if (rc) return rc;
+    if (!X || !y_out || n < 0) return fail(JK_ERR_ARG, "bad arguments");
+    if (n == 0) return JK_OK;
+    JkRouterDev d;
+    router_dev_from_blob(*w, d);
+    JkRouterDev *dd = nullptr;
+    CK(cudaMalloc(&dd, sizeof d));
+    cudaMemcpy(dd, &d, sizeof d, cudaMemcpyHostToDevice);
+    jk_mlp_forward_kernel<<<(unsigned)((n + 255) / 256), 256>>>(dd, X, (long long)n, y_out);
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(dd);
+    if (e != cudaSuccess) return fail(JK_ERR_CUDA, "router forward: %s", cudaGetErrorString(e));
+    return JK_OK;
+}
+
+int jk_router_gradient(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
+                       float *grad_host, double *loss)
+{
+    int rc = check_blob(w);
+    if (rc) return rc;
+    if (!X || !y || !grad_host || !loss || n < 1 || n > (1 << 30) || !(quantile > 0 && quantile < 1))
+        return fail(JK_ERR_ARG, "bad arguments");
+    float *th = nullptr, *mu = nullptr, *isd = nullptr, *g = nullptr;
+    double *l = nullptr;
+    long long *idx = nullptr;
+    std::vector<long long> iota((size_t)n);
+    for (int64_t i = 0; i < n; ++i) iota[i] = i;
+    auto cleanup = [&]() { cudaFree(th); cudaFree(mu); cudaFree(isd); cudaFree(g); cudaFree(l); cudaFree(idx); };
+    struct Guard { std::function<void()> f; ~Guard() { f(); } } guard{cleanup};
+    CK(cudaMalloc(&th, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMalloc(&mu, sizeof(float) * 16));
+    CK(cudaMalloc(&isd, sizeof(float) * 16));
+    CK(cudaMalloc(&g, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMalloc(&l, sizeof(double)));
+    CK(cudaMalloc(&idx, sizeof(long long) * n));
+    CK(cudaMemcpy(th, w->theta, sizeof(float) * JK_RT_NPARAM, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(mu, w->mu, sizeof(float) * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(isd, w->isd, sizeof(float) * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(idx, iota.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemset(g, 0, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMemset(l, 0, sizeof(double)));
+    const size_t smem = 2 * JK_RT_NPARAM * sizeof(float);
+    jk_mlp_grad_kernel<<<(unsigned)((n + 255) / 256), 256, smem>>>(th, mu, isd, X, y, (long long)n, idx, (int)n, 0ull,
+                                                                 quantile, g, l);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(grad_host, g, sizeof(float) * JK_RT_NPARAM, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(loss, l, sizeof(double), cudaMemcpyDeviceToHost));
+    return JK_OK;
+}
+
+int jk_router_train(const float *X, const float *y, int64_t n, const jk_train_opts *opts, jk_router_blob *out,
+                    jk_train_stats *stats)
+{
+    if (!X || !y || !opts || !out || n < 2) return fail(JK_ERR_ARG, "bad arguments");
+    if (opts->steps < 1 || opts->batch < 1 || opts->batch > (1 << 22) || !(opts->lr > 0) ||
+        !(opts->quantile > 0 && opts->quantile < 1))
+        return fail(JK_ERR_ARG, "bad training options");
+    auto t0 = std::chrono::steady_clock::now();
+    // feature normalisation from the data
+    std::vector<float> hx((size_t)n * JK_RT_NIN);
+    CK(cudaMemcpy(hx.data(), X, sizeof(float) * hx.size(), cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof(*out));
+    out->magic = JK_ROUTER_MAGIC;
+    out->version = 1;
+    out->quantile = opts->quantile;
+    for (int k = 0; k < 16; ++k) { out->mu[k] = 0.f; out->isd[k] = 0.f; }
+    for (int k = 0; k < JK_RT_NIN; ++k) {
+        double m = 0, v = 0;
+        for (int64_t i = 0; i < n; ++i) m += hx[i * JK_RT_NIN + k];
+        m /= n;
+        for (int64_t i = 0; i < n; ++i) { double d = hx[i * JK_RT_NIN + k] - m; v += d * d; }
+        v /= n;
+        out->mu[k] = (float)m;
+        out->isd[k] = (float)(1.0 / std::max(std::sqrt(v), 1e-6));
+    }
+    // initial weights: uniform(-a, a), a = sqrt(6 / (fan_in + fan_out)); biases 0
+    unsigned long long z = opts->seed ^ 0x6a09e667f3bcc909ull;
+    auto rnd = [&]() {
+        z += 0x9e3779b97f4a7c15ull;
+        unsigned long long r = z;
+        r = (r ^ (r >> 30)) * 0xbf58476d1ce4e5b9ull;
+        r = (r ^ (r >> 27)) * 0x94d049bb133111ebull;
+        r ^= r >> 31;
+        return (double)(r >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    };
+    float *th = out->theta;
+    for (int i = 0; i < JK_RT_NPARAM; ++i) th[i] = 0.f;
+    const double a1 = std::sqrt(6.0 / (JK_RT_NIN + JK_RT_NH)), a2 = std::sqrt(6.0 / (2 * JK_RT_NH)),
+                 a3 = std::sqrt(6.0 / (JK_RT_NH + 1));
+    for (int i = 0; i < JK_RT_NIN; ++i)
+        for (int o = 0; o < JK_RT_NH; ++o) th[JK_RT_OFF_W1 + i * JK_RT_NH + o] = (float)(a1 * rnd());
+    for (int i = 0; i < JK_RT_NH * JK_RT_NH; ++i) th[JK_RT_OFF_W2 + i] = (float)(a2 * rnd());
+    for (int i = 0; i < JK_RT_NH; ++i) th[JK_RT_OFF_W3 + i] = (float)(a3 * rnd());
+    {
+        std::vector<float> hy((size_t)n);
+        CK(cudaMemcpy(hy.data(), y, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        double m = 0;
+        for (auto v : hy) m += v;
+        th[JK_RT_OFF_B3] = (float)(m / n);
+    }
+    float *dth = nullptr, *mu = nullptr, *isd = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
+    double *lh = nullptr;
+    auto cleanup = [&]() { cudaFree(dth); cudaFree(mu); cudaFree(isd); cudaFree(g); cudaFree(m1); cudaFree(m2); cudaFree(lh); };
+    struct Guard { std::function<void()> f; ~Guard() { f(); } } guard{cleanup};
+    CK(cudaMalloc(&dth, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMalloc(&g, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMalloc(&m1, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMalloc(&m2, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMalloc(&mu, sizeof(float) * 16));
+    CK(cudaMalloc(&isd, sizeof(float) * 16));
+    CK(cudaMalloc(&lh, sizeof(double) * opts->steps));
+    CK(cudaMemcpy(dth, th, sizeof(float) * JK_RT_NPARAM, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(mu, out->mu, sizeof(float) * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(isd, out->isd, sizeof(float) * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemset(m1, 0, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMemset(m2, 0, sizeof(float) * JK_RT_NPARAM));
+    CK(cudaMemset(lh, 0, sizeof(double) * opts->steps));
+    const size_t smem = 2 * JK_RT_NPARAM * sizeof(float);
+    const unsigned gb = (unsigned)((opts->batch + 255) / 256);
+    for (int step = 1; step <= opts->steps; ++step) {
+        CK(cudaMemsetAsync(g, 0, sizeof(float) * JK_RT_NPARAM));
+        jk_mlp_grad_kernel<<<gb, 256, smem>>>(dth, mu, isd, X, y, (long long)n, nullptr, opts->batch,
+                                               opts->seed * 1000003ull + (unsigned long long)step, opts->quantile, g,
+                                               lh + (step - 1));
+        jk_adam_kernel<<<(JK_RT_NPARAM + 255) / 256, 256>>>(dth, g, m1, m2, step, opts->lr, 0.9f, 0.999f, 1e-8f);
+    }
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(th, dth, sizeof(float) * JK_RT_NPARAM, cudaMemcpyDeviceToHost));
+    std::vector<double> hl(opts->steps);
+    CK(cudaMemcpy(hl.data(), lh, sizeof(double) * opts->steps, cudaMemcpyDeviceToHost));
+    if (stats) {
+        const int w = std::min(50, opts->steps);
+        double a = 0, b = 0;
+        for (int i = 0; i < w; ++i) { a += hl[i]; b += hl[opts->steps - 1 - i]; }
+        stats->loss_first = a / w;
+        stats->loss_last = b / w;
+        stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return JK_OK;
+}
+
 int jk_profile(jk_handle *h, jk_launch_prof *out, int32_t max, int32_t *n)
 {
     if (!h || !n || (max > 0 && !out)) return fail(JK_ERR_ARG, "NULL argument");
@@ -1340,7 +1612,7 @@ int jk_measure_peak(int32_t which, double ms, double *flops_per_s)
 }
 
 int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na, int32_t nb, int32_t nc,
-                     int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32,
+                     int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32, int32_t mode,
                      int32_t *threads_per_quartet, double *compile_ms)
 {
     if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > JK_LMAX || lb > JK_LMAX || lc > JK_LMAX || ld > JK_LMAX)
@@ -1349,10 +1621,12 @@ int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na,
         nd > JK_NPRIM_MAX)
         return fail(JK_ERR_UNSUPPORTED, "primitive count out of range");
     if (n_dm < 1 || n_dm > JK_NDM_MAX || (!with_j && !with_k)) return fail(JK_ERR_ARG, "bad n_dm or flags");
+    if (mode < 0 || mode > 2 || (mode == 2 && fp32)) return fail(JK_ERR_ARG, "bad mode");
     KSpec s;
     s.kind = 0;
     s.la = la; s.lb = lb; s.lc = lc; s.ld = ld; s.na = na; s.nb = nb; s.nc = nc; s.nd = nd;
     s.ndm = n_dm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0; s.fp32 = fp32 ? 1 : 0;
+    s.mode = mode;
     choose_fragments(s, false);
     if (threads_per_quartet) *threads_per_quartet = s.G();
     try {

@@ -360,11 +360,14 @@ template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassA
 // Keep (bra, ket j) iff lo < Q_ab Q_cd Dmax <= hi; `stop` when even the
 // molecule's largest density element cannot lift this ket (and every later
 // one, kets being sorted by Q) above lo.
-__device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
-                                          const double *dmx, double dmol, int j, int ke, bool &sig, bool &stop)
+template <int MODE>
+__device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkPairFeat &braf,
+                                          const JkMol &mol, const double *dmx, double dmol, int j, int ke,
+                                          bool &sig, bool &stop, bool &band)
 {
     sig = false;
     stop = false;
+    band = false;
     if (j >= ke) return;
     const double bq = bra.Q * args.ket[j].Q;
     if (bq * dmol <= args.lo) { stop = true; return; }
@@ -381,6 +384,41 @@ __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair 
     }
     const double B = bq * dm;
     sig = (B > args.lo) && (B <= args.hi);
+    if (MODE == 1 && sig && B > args.tau && B <= args.band_hi) {
+        const bool to32 = jk_router_to_fp32(args.router, braf, args.ket_feat[j], B, dm, args.tau);
+        sig = (args.tier == 1) ? to32 : !to32;
+        band = sig;
+    }
+}
+
+// Density factor of a quartet (the same lookups as jk_screen).
+__device__ __forceinline__ double jk_quartet_dmax(const JkClassArgs &args, const JkPair &bra, const JkPair &ket,
+                                                  const JkMol &mol, const double *dmx)
+{
+    if (!args.use_dmax) return 1.0;
+    const int a = bra.a_loc, b = bra.b_loc, c = ket.a_loc, d = ket.b_loc, ns = mol.nsh;
+    double dm = 0.0;
+    if (args.with_j) dm = fmax(__ldg(dmx + a * ns + b), __ldg(dmx + c * ns + d));
+    if (args.with_k) {
+        dm = fmax(dm, fmax(__ldg(dmx + a * ns + c), __ldg(dmx + a * ns + d)));
+        dm = fmax(dm, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
+    }
+    return dm;
+}
+
+// MODE 2: one training sample (features, label) for a band quartet, written
+// by the group's first thread. tmax is the group's max |T|.
+__device__ __forceinline__ void jk_log_sample(const JkClassArgs &args, const JkPair &bra, const JkPair &ket,
+                                              const JkPairFeat &braf, const JkPairFeat &ketf, double dm, double tmax)
+{
+    const double B = bra.Q * ket.Q * dm;
+    if (!(B > args.tau && B <= args.band_hi)) return;
+    const unsigned long long idx = atomicAdd(args.log_n, 1ull);
+    if ((long long)idx >= args.log_cap) return;
+    float x[JK_RT_NIN];
+    jk_router_features(braf, ketf, B, dm, args.tau, x);
+    for (int i = 0; i < JK_RT_NIN; ++i) args.log_x[idx * JK_RT_NIN + i] = x[i];
+    args.log_y[idx] = (float)log10(fmax(tmax, 1e-300) / (bra.Q * ket.Q));
 }
 
 // ------------------------------------------ contraction with the density
@@ -517,7 +555,7 @@ __device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol 
 // Persistent: warps (or, for groups of more than 32 threads, whole CTAs)
 // take bra pairs from a global counter until none are left.
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
-          int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R>
+          int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R, int MODE>
 __global__ void __launch_bounds__(JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G <= 32 ? 128
                                   : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G + 31) / 32) * 32)
 jk_class_kernel(const JkClassArgs args)
@@ -552,6 +590,8 @@ jk_class_kernel(const JkClassArgs args)
             const double *dmx = args.dmax + mol.dmax_off;
             const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
             const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+            JkPairFeat braf;
+            if (MODE != 0) braf = args.bra_feat[item];
             R jab[NDM][FA][FB];
 #pragma unroll
             for (int m = 0; m < NDM; ++m)
@@ -559,12 +599,13 @@ jk_class_kernel(const JkClassArgs args)
                 for (int i = 0; i < FA; ++i)
 #pragma unroll
                     for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
-            unsigned long long nq = 0;
+            unsigned long long nq = 0, nband = 0;
             for (int base = kb; base < ke; base += 32) {
-                bool sig, stop;
-                jk_screen(args, bra, mol, dmx, dmol, base + lane, ke, sig, stop);
+                bool sig, stop, band;
+                jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band);
                 unsigned mask = __ballot_sync(0xffffffffu, sig);
                 nq += __popc(mask);
+                if (MODE == 1) nband += __popc(__ballot_sync(0xffffffffu, band));
                 while (mask) {
                     int myket = -1;
                     if (active) {
@@ -586,6 +627,15 @@ jk_class_kernel(const JkClassArgs args)
                         if (args.same_class && myket == item) f *= (R)0.5;
                         jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
                                                                      ket.b_ao + gd * FD, jab);
+                        if (MODE == 2) {
+                            double tm = 0.0;
+#pragma unroll
+                            for (int k = 0; k < S::EPT; ++k) tm = fmax(tm, fabs((double)T[k]));
+                            for (int q = 0; q < G; ++q) tm = fmax(tm, __shfl_sync(gmask, tm, (gw * G + q) & 31));
+                            if (tg == 0)
+                                jk_log_sample(args, bra, ket, braf, args.ket_feat[myket],
+                                              jk_quartet_dmax(args, bra, ket, mol, dmx), tm);
+                        }
                     }
                     __syncwarp();
                 }
@@ -595,6 +645,7 @@ jk_class_kernel(const JkClassArgs args)
             if (lane == 0 && nq) {
                 atomicAdd(args.stats, nq);
                 atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+                if (nband) atomicAdd(args.stats + 2, nband);
             }
         }
     } else {
@@ -622,6 +673,8 @@ jk_class_kernel(const JkClassArgs args)
             const double *dmx = args.dmax + mol.dmax_off;
             const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
             const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+            JkPairFeat braf;
+            if (MODE != 0) braf = args.bra_feat[item];
             R jab[NDM][FA][FB];
 #pragma unroll
             for (int m = 0; m < NDM; ++m)
@@ -629,14 +682,15 @@ jk_class_kernel(const JkClassArgs args)
                 for (int i = 0; i < FA; ++i)
 #pragma unroll
                     for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
-            unsigned long long nq = 0;
+            unsigned long long nq = 0, nband = 0;
             for (int base = kb; base < ke; base += 32) {
                 if (threadIdx.x < 32) {
-                    bool sig, stop;
-                    jk_screen(args, bra, mol, dmx, dmol, base + lane, ke, sig, stop);
+                    bool sig, stop, band;
+                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band);
                     const unsigned msk = __ballot_sync(0xffffffffu, sig);
                     const int anystop = __any_sync(0xffffffffu, stop);
-                    if (lane == 0) { s_mask = msk; s_stop = anystop; }
+                    const unsigned bmsk = __ballot_sync(0xffffffffu, band);
+                    if (lane == 0) { s_mask = msk; s_stop = anystop; nband += __popc(bmsk); }
                 }
                 __syncthreads();
                 unsigned mask = s_mask;
@@ -659,6 +713,23 @@ jk_class_kernel(const JkClassArgs args)
                         jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
                                                                      ket.b_ao + gd * FD, jab);
                     }
+                    if (MODE == 2) {
+                        __shared__ double s_tm[32];
+                        double tm = 0.0;
+                        if (act) {
+#pragma unroll
+                            for (int k = 0; k < S::EPT; ++k) tm = fmax(tm, fabs((double)T[k]));
+                        }
+                        for (int o = 16; o > 0; o >>= 1) tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+                        if (lane == 0) s_tm[threadIdx.x >> 5] = tm;
+                        __syncthreads();
+                        if (threadIdx.x == 0) {
+                            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tm = fmax(tm, s_tm[w]);
+                            jk_log_sample(args, bra, ket, braf, args.ket_feat[myket],
+                                          jk_quartet_dmax(args, bra, ket, mol, dmx), tm);
+                        }
+                        __syncthreads();
+                    }
                 }
                 if (stop) break;
             }
@@ -666,6 +737,7 @@ jk_class_kernel(const JkClassArgs args)
             if (threadIdx.x == 0 && nq) {
                 atomicAdd(args.stats, nq);
                 atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+                if (nband) atomicAdd(args.stats + 2, nband);
             }
         }
     }

@@ -45,6 +45,9 @@ struct JkMol {
     long long dmax_off;  // offset of this molecule's nsh x nsh block-max table
 };
 
+struct JkRouterDev;
+struct JkPairFeat;
+
 // Arguments of one class-pair launch (passed by value).
 struct JkClassArgs {
     const JkPair *bra;           // pairs of the bra class
@@ -59,7 +62,7 @@ struct JkClassArgs {
     const double *rys64;         // FP64 Rys tables
     const float *rys32;          // FP32 Rys tables
     int *work;                   // work counter (zeroed before the launch)
-    unsigned long long *stats;   // [0] quartets, [1] primitive quartets
+    unsigned long long *stats;   // [0] quartets, [1] primitive quartets, [2] routed band quartets
     int *err;                    // device error word
     double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi
     int nbra;
@@ -67,6 +70,17 @@ struct JkClassArgs {
     int with_j, with_k;          // which outputs (and density blocks) to use
     int use_dmax;                // 0: screen with Dmax := 1
     int ndm;
+    // learned router (MODE 1) and label logging (MODE 2)
+    const JkPairFeat *bra_feat;  // aligned with bra / ket
+    const JkPairFeat *ket_feat;
+    const JkRouterDev *router;
+    double tau;                  // band (tau, band_hi]
+    double band_hi;
+    int tier;                    // 0: this launch is the FP64 tier, 1: FP32
+    float *log_x;                // MODE 2: features (12 per sample)
+    float *log_y;                // MODE 2: labels
+    unsigned long long *log_n;   // MODE 2: samples written (may exceed log_cap)
+    long long log_cap;
 };
 
 // Arguments of the Schwarz (diagonal-quartet) launch of one pair class.

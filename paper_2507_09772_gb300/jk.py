@@ -24,8 +24,13 @@ PRECISION = {"fp64": JK_PREC_FP64, "mixed": JK_PREC_MIXED, "routed": JK_PREC_MIX
 
 # every function include/jk.h declares
 EXPORTED = ["jk_init", "jk_init_batch", "jk_build", "jk_build_batch", "jk_set_option",
-            "jk_get_option", "jk_info", "jk_schwarz", "jk_destroy", "jk_profile", "jk_measure_peak",
+            "jk_get_option", "jk_info", "jk_schwarz", "jk_destroy", "jk_router_collect", "jk_router_train",
+            "jk_router_forward", "jk_router_gradient", "jk_router_load", "jk_profile", "jk_measure_peak",
             "jk_compile_class", "jk_last_error"]
+
+ROUTER_NIN = 12
+ROUTER_NPARAM = 5313
+ROUTER_MAGIC = 0x4a4b5254
 
 
 class JKError(RuntimeError):
@@ -58,6 +63,34 @@ class JkLaunchProf(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class JkRouterBlob(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32),
+                ("mu", ctypes.c_float * 16), ("isd", ctypes.c_float * 16),
+                ("theta", ctypes.c_float * ROUTER_NPARAM), ("margin", ctypes.c_float),
+                ("quantile", ctypes.c_float)]
+
+    def to_bytes(self) -> bytes:
+        return ctypes.string_at(ctypes.addressof(self), ctypes.sizeof(self))
+
+    @classmethod
+    def from_bytes(cls, b: bytes):
+        blob = cls()
+        ctypes.memmove(ctypes.addressof(blob), b, ctypes.sizeof(cls))
+        return blob
+
+
+class JkTrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("quantile", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class JkTrainStats(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -85,8 +118,15 @@ def load_library() -> ctypes.CDLL:
     lib.jk_info.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.jk_schwarz.argtypes = [vp, dp]
     lib.jk_destroy.argtypes = [vp]
-    lib.jk_compile_class.argtypes = [i32] * 12 + [P(i32), dp]
+    lib.jk_compile_class.argtypes = [i32] * 13 + [P(i32), dp]
     lib.jk_profile.argtypes = [vp, P(JkLaunchProf), i32, P(i32)]
+    lib.jk_router_collect.argtypes = [vp, P(vp), i32, ctypes.c_double, P(vp), P(vp), vp, vp, ctypes.c_int64,
+                                      P(ctypes.c_int64), vp]
+    lib.jk_router_train.argtypes = [vp, vp, ctypes.c_int64, P(JkTrainOpts), P(JkRouterBlob), P(JkTrainStats)]
+    lib.jk_router_forward.argtypes = [P(JkRouterBlob), vp, ctypes.c_int64, vp]
+    lib.jk_router_gradient.argtypes = [P(JkRouterBlob), vp, vp, ctypes.c_int64, ctypes.c_float,
+                                       P(ctypes.c_float), P(ctypes.c_double)]
+    lib.jk_router_load.argtypes = [vp, P(JkRouterBlob)]
     lib.jk_measure_peak.argtypes = [i32, ctypes.c_double, dp]
     lib.jk_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -203,6 +243,45 @@ def jk_destroy(h):
     _check(load_library().jk_destroy(h))
 
 
+def jk_router_collect(h, Ds, n_dm, cutoff, Js, Ks, X, y, stream=None) -> int:
+    """FP64 build that also writes band-quartet features X (cap x 12) and
+    labels y (cap) (torch float32 CUDA tensors); returns the number seen."""
+    n = len(Ds)
+    arr = ctypes.c_void_p * n
+    cnt = ctypes.c_int64()
+    _check(load_library().jk_router_collect(h, arr(*[_ptr(d) for d in Ds]), int(n_dm), float(cutoff),
+                                            arr(*[_ptr(j) for j in Js]), arr(*[_ptr(k) for k in Ks]),
+                                            _ptr(X), _ptr(y), int(y.shape[0]), ctypes.byref(cnt),
+                                            _stream_ptr(stream)))
+    return cnt.value
+
+
+def jk_router_train(X, y, steps=2000, batch=4096, lr=2e-3, quantile=0.9, seed=1):
+    """Train on the device (X: n x 12, y: n, torch float32 CUDA). Returns (blob, stats)."""
+    opts = JkTrainOpts(int(steps), int(batch), float(lr), float(quantile), int(seed))
+    blob = JkRouterBlob()
+    st = JkTrainStats()
+    _check(load_library().jk_router_train(_ptr(X), _ptr(y), int(y.shape[0]), ctypes.byref(opts),
+                                          ctypes.byref(blob), ctypes.byref(st)))
+    return blob, st.as_dict()
+
+
+def jk_router_forward(blob, X, y_out):
+    _check(load_library().jk_router_forward(ctypes.byref(blob), _ptr(X), int(X.shape[0]), _ptr(y_out)))
+
+
+def jk_router_gradient(blob, X, y, quantile):
+    g = (ctypes.c_float * ROUTER_NPARAM)()
+    loss = ctypes.c_double()
+    _check(load_library().jk_router_gradient(ctypes.byref(blob), _ptr(X), _ptr(y), int(y.shape[0]),
+                                             float(quantile), g, ctypes.byref(loss)))
+    return np.frombuffer(g, dtype=np.float32).copy(), loss.value
+
+
+def jk_router_load(h, blob):
+    _check(load_library().jk_router_load(h, ctypes.byref(blob)))
+
+
 def jk_profile(h):
     """Per-launch records of the last profiled build (option "profile" = 1)."""
     n = ctypes.c_int32()
@@ -219,10 +298,10 @@ def jk_measure_peak(which: str = "fp64", ms: float = 200.0) -> float:
     return v.value
 
 
-def jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm=1, with_j=1, with_k=1, fp32=0):
+def jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm=1, with_j=1, with_k=1, fp32=0, mode=0):
     g = ctypes.c_int32()
     ms = ctypes.c_double()
-    _check(load_library().jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm, with_j, with_k, fp32,
+    _check(load_library().jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm, with_j, with_k, fp32, mode,
                                            ctypes.byref(g), ctypes.byref(ms)))
     return g.value, ms.value
 
@@ -265,6 +344,9 @@ class JK:
 
     def get_option(self, key):
         return jk_get_option(self.h, key)
+
+    def load_router(self, blob):
+        jk_router_load(self.h, blob)
 
     def build(self, D, with_j=True, with_k=True, cutoff=1e-13, precision="fp64", J=None, K=None,
               stream=None, stats=False):

@@ -71,6 +71,8 @@ def test_bad_shell_fields_are_rejected(lib):
 def test_class_kernels_compile_for_sm103a(lib, cls, tmp_path, monkeypatch):
     monkeypatch.setenv("JK_KERNEL_CACHE", str(tmp_path))
     g, ms = jk.jk_compile_class(*cls[:8], n_dm=1, with_j=1, with_k=1, fp32=cls[8])
+    g2, _ = jk.jk_compile_class(*cls[:8], n_dm=1, with_j=1, with_k=1, fp32=cls[8], mode=1)
+    assert g2 == g
     assert g >= 1
     assert any(p.suffix == ".bin" for p in tmp_path.iterdir())
 
