@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-probe", action="store_true", help="skip the FMA peak probes (profiling runs)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
+    ap.add_argument("--form-steps", type=int, default=2)
+    ap.add_argument("--tau32", type=float, default=1e-7)
     return ap.parse_args()
 
 
@@ -166,6 +170,72 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets):
+    """Mixed (Schwarz x Dmax tiering) and routed (learned router in the band)
+    builds of the same batch, timed like the FP64 steps, with their largest
+    deviation from the FP64 result over every element of J and K."""
+    import torch
+    from paper_2507_09772_gb300 import jk
+
+    Jref = [j.clone() for j in Js]
+    Kref = [k.clone() for k in Ks]
+    eng.set_option("tau32", args.tau32)
+    out = {"fp64": {"ms_per_step": fp64_ms, "quartets_per_s": fp64_quartets / (fp64_ms * 1e-3)},
+           "tau32": args.tau32, "accuracy_reference": "the FP64 build of this run (full matrices)"}
+
+    def timed(precision):
+        _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)  # warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sts = []
+        e0.record(stream)
+        for _ in range(args.form_steps):
+            flush.fill_(1)
+            _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)
+            sts.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.form_steps
+        dj = max(float((a - b).abs().max()) for a, b in zip(Js, Jref))
+        dk = max(float((a - b).abs().max()) for a, b in zip(Ks, Kref))
+        st = sts[-1]
+        q = st["quartets_fp64"] + st["quartets_fp32"]
+        return {"ms_per_step": ms, "quartets_per_s": q / (ms * 1e-3), "speedup_vs_fp64": fp64_ms / ms,
+                "max_abs_dJ": dj, "max_abs_dK": dk, "within_1e-8": bool(max(dj, dk) <= 1e-8),
+                "fp32_fraction": st["quartets_fp32"] / max(1, q), "quartets_routed": st["quartets_routed"],
+                "same_quartets_as_fp64": bool(q == fp64_quartets)}
+
+    out["mixed"] = timed("mixed")
+    # router: labels from an FP64 logging build of the first 8 molecules
+    # (a separate handle), trained on the GPU, then routed builds of the batch
+    t0 = time.perf_counter()
+    sub = mols[:8]
+    eng_l = jk.JK(sub)
+    eng_l.set_option("tau32", args.tau32)
+    Dl = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in sub]
+    Jl = [torch.empty_like(d) for d in Dl]
+    Kl = [torch.empty_like(d) for d in Dl]
+    cap = 2_000_000
+    X = torch.empty((cap, 12), dtype=torch.float32, device="cuda")
+    y = torch.empty(cap, dtype=torch.float32, device="cuda")
+    n = min(cap, jk.jk_router_collect(eng_l.h, Dl, 1, args.cutoff, Jl, Kl, X, y))
+    eng_l.close()
+    blob, tst = jk.jk_router_train(X[:n], y[:n], steps=1500, batch=8192, lr=2e-3, quantile=0.95, seed=1)
+    train_s = time.perf_counter() - t0
+    eng.load_router(blob)
+    r = timed("routed")
+    r.update({"train_samples": int(n), "train_s": train_s, "train_loss_first": tst["loss_first"],
+              "train_loss_last": tst["loss_last"]})
+    out["routed"] = r
+    # leave the FP64 result in Js, Ks
+    for a, b in zip(Js, Jref):
+        a.copy_(b)
+    for a, b in zip(Ks, Kref):
+        a.copy_(b)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -246,7 +316,8 @@ def run_ours(args):
     dom_ms = dom["ms"] / dom["launches"]
     dom_flops = dom["flops_model"] / dom["launches"]
     peak = PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL
-    probe = jk.jk_measure_peak("fp64" if dom["tier"] == 0 else "fp32", 100.0)
+    probe = (jk.jk_measure_peak("fp64" if dom["tier"] == 0 else "fp32", 100.0) if not args.no_probe
+             else (PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL))
     roofline = {
         "bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
         "frac": dom_flops / (dom_ms * 1e-3) / peak, "traffic": None,
@@ -300,6 +371,11 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": float(t_e.item()) / args.steps}
 
+    # the accelerated forms on the same inputs, against this FP64 build
+    forms = None
+    if not args.no_forms and args.precision == "fp64":
+        forms = run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, ms_max / args.steps, quartets / args.steps)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_oracle_sample(mols, args.cpu_seconds, args.cutoff)
@@ -322,14 +398,15 @@ def run_ours(args):
             "path_fp64_roofline": path_fp64,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "forms": forms,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": int(launches),
             "init_ms": 1e3 * init_s,
             "first_build_s": first_s,
             "compile_ms": eng.get_option("compile_ms"),
-            "peak_probe_fp64_tflops": jk.jk_measure_peak("fp64", 100.0) / 1e12,
-            "peak_probe_fp32_tflops": jk.jk_measure_peak("fp32", 100.0) / 1e12,
+            "peak_probe_fp64_tflops": None if args.no_probe else jk.jk_measure_peak("fp64", 100.0) / 1e12,
+            "peak_probe_fp32_tflops": None if args.no_probe else jk.jk_measure_peak("fp32", 100.0) / 1e12,
             "top_kernels": sorted(
                 [{"class": "(%d%d|%d%d)/%d%d%d%d" % (v["la"], v["lb"], v["lc"], v["ld"], v["na"], v["nb"], v["nc"], v["nd"]),
                   "tier": v["tier"], "ms_per_step": v["ms"] / args.steps, "share": v["ms"] / ms_total,
