@@ -207,6 +207,29 @@ int jk_router_forward(const jk_router_blob *w, const float *X, int64_t n, float 
 int jk_router_gradient(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
                        float *grad_host, double *loss);
 
+/* The same result as jk_router_gradient (mean pinball loss and gradient over
+ * n rows; X, y on the device; grad_host and loss on the host), from a variant
+ * that makes no device allocation. The paper has no counterpart; this is for
+ * callers that cannot call cudaMalloc: code running while a CUDA stream is
+ * being captured (where cudaMalloc is not allowed), and applications that
+ * hand every byte of device memory to their own allocator and forbid
+ * libraries from allocating more.
+ *   - Scratch: one fixed __device__ array in the library (about 560 KB,
+ *     present on every GPU that loads the library until the process exits),
+ *     holding the weight copies, the row list and the accumulators. At most
+ *     JK_NOALLOC_MAX_ROWS rows per call; larger n returns JK_ERR_UNSUPPORTED
+ *     and touches nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and clears the accumulators itself; calls
+ *     whose work overlaps on the GPU (other streams, other host threads)
+ *     race on it. Work is queued on `stream` and the call returns after
+ *     synchronising it. */
+#define JK_NOALLOC_MAX_ROWS 65536
+int jk_router_gradient_noalloc(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
+                               float *grad_host, double *loss, void *stream);
+
 /* Install router weights on a handle (enables JK_PREC_MIXED_ROUTED). */
 int jk_router_load(jk_handle *h, const jk_router_blob *w);
 

@@ -1269,8 +1269,85 @@ int check_blob(const jk_router_blob *w)
 
 }  // namespace
 
+// ============================================= no-allocation gradient variant
+// Fixed device scratch for jk_router_gradient_noalloc: the weight copies, the
+// row list and the two accumulators of jk_mlp_grad_kernel live in one
+// file-scope __device__ array (about 560 KB, held by every GPU that loads this
+// library until the process exits) instead of buffers from cudaMalloc.
+struct JkNoAllocScratch {   // JK_NOALLOC_MAX_ROWS comes from jk.h
+    float theta[JK_RT_NPARAM];
+    float mu[16], isd[16];
+    float grad[JK_RT_NPARAM];
+    double loss;
+    long long idx[JK_NOALLOC_MAX_ROWS];
+};
+static __device__ __align__(256) unsigned char jk_noalloc_scratch[sizeof(JkNoAllocScratch)];
+
+__global__ void jk_noalloc_iota_kernel(long long *idx, long long n)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) idx[t] = t;
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {};
+
+// Device address of the scratch array on the current device. Host code may
+// not use the array's name as an address, so it is looked up once per device
+// (with that device current) and cached.
+int noalloc_scratch(JkNoAllocScratch **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(JK_ERR_UNSUPPORTED, "device ordinal %d above 63", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, jk_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(JK_ERR_CUDA, "cudaGetSymbolAddress(jk_noalloc_scratch): %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (JkNoAllocScratch *)g_noalloc_ptr[dev];
+    return JK_OK;
+}
+}  // namespace
+
 // ===================================================================== ABI
 extern "C" {
+
+int jk_router_gradient_noalloc(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
+                               float *grad_host, double *loss, void *stream)
+{
+    int rc = check_blob(w);
+    if (rc) return rc;
+    if (!X || !y || !grad_host || !loss || n < 1 || !(quantile > 0 && quantile < 1))
+        return fail(JK_ERR_ARG, "bad arguments");
+    if (n > JK_NOALLOC_MAX_ROWS)
+        return fail(JK_ERR_UNSUPPORTED, "n = %lld rows exceeds the fixed scratch of jk_router_gradient_noalloc (%d rows)",
+                    (long long)n, JK_NOALLOC_MAX_ROWS);
+    JkNoAllocScratch *S = nullptr;
+    if ((rc = noalloc_scratch(&S))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(S->theta, w->theta, sizeof(float) * JK_RT_NPARAM, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->mu, w->mu, sizeof(float) * 16, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->isd, w->isd, sizeof(float) * 16, cudaMemcpyHostToDevice, st));
+    // the accumulators keep the previous call's values: clear them
+    CK(cudaMemsetAsync(S->grad, 0, sizeof(float) * JK_RT_NPARAM, st));
+    CK(cudaMemsetAsync(&S->loss, 0, sizeof(double), st));
+    jk_noalloc_iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S->idx, (long long)n);
+    const size_t smem = 2 * JK_RT_NPARAM * sizeof(float);
+    jk_mlp_grad_kernel<<<(unsigned)((n + 255) / 256), 256, smem, st>>>(S->theta, S->mu, S->isd, X, y, (long long)n,
+                                                                       S->idx, (int)n, 0ull, quantile, S->grad,
+                                                                       &S->loss);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(grad_host, S->grad, sizeof(float) * JK_RT_NPARAM, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(loss, &S->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return JK_OK;
+}
+
 
 int jk_init(const jk_shell *shells, int32_t nshell, const double *coords, int32_t natm, const double *exps,
             const double *coeffs, int32_t nprim_total, jk_handle **out)

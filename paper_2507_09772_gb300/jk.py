@@ -25,7 +25,8 @@ PRECISION = {"fp64": JK_PREC_FP64, "mixed": JK_PREC_MIXED, "routed": JK_PREC_MIX
 # every function include/jk.h declares
 EXPORTED = ["jk_init", "jk_init_batch", "jk_build", "jk_build_batch", "jk_set_option",
             "jk_get_option", "jk_info", "jk_schwarz", "jk_destroy", "jk_router_collect", "jk_router_train",
-            "jk_router_forward", "jk_router_gradient", "jk_router_load", "jk_profile", "jk_measure_peak",
+            "jk_router_forward", "jk_router_gradient", "jk_router_gradient_noalloc", "jk_router_load",
+            "jk_profile", "jk_measure_peak",
             "jk_compile_class", "jk_last_error"]
 
 ROUTER_NIN = 12
@@ -127,6 +128,8 @@ def load_library() -> ctypes.CDLL:
     lib.jk_router_gradient.argtypes = [P(JkRouterBlob), vp, vp, ctypes.c_int64, ctypes.c_float,
                                        P(ctypes.c_float), P(ctypes.c_double)]
     lib.jk_router_load.argtypes = [vp, P(JkRouterBlob)]
+    lib.jk_router_gradient_noalloc.argtypes = [P(JkRouterBlob), vp, vp, ctypes.c_int64, ctypes.c_float,
+                                               P(ctypes.c_float), P(ctypes.c_double), vp]
     lib.jk_measure_peak.argtypes = [i32, ctypes.c_double, dp]
     lib.jk_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -275,6 +278,17 @@ def jk_router_gradient(blob, X, y, quantile):
     loss = ctypes.c_double()
     _check(load_library().jk_router_gradient(ctypes.byref(blob), _ptr(X), _ptr(y), int(y.shape[0]),
                                              float(quantile), g, ctypes.byref(loss)))
+    return np.frombuffer(g, dtype=np.float32).copy(), loss.value
+
+
+def jk_router_gradient_noalloc(blob, X, y, quantile, stream=None):
+    """Same result as jk_router_gradient from the variant that allocates no
+    device memory (fixed library scratch; see include/jk.h)."""
+    g = (ctypes.c_float * ROUTER_NPARAM)()
+    loss = ctypes.c_double()
+    _check(load_library().jk_router_gradient_noalloc(ctypes.byref(blob), _ptr(X), _ptr(y), int(y.shape[0]),
+                                                     float(quantile), g, ctypes.byref(loss),
+                                                     _stream_ptr(stream)))
     return np.frombuffer(g, dtype=np.float32).copy(), loss.value
 
 
