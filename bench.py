@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
     ap.add_argument("--form-steps", type=int, default=2)
     ap.add_argument("--tau32", type=float, default=1e-7)
+    ap.add_argument("--graph", type=int, default=1, help="replay each build as one CUDA graph")
+    ap.add_argument("--branches", type=int, default=4, help="class kernels forked over this many graph branches")
     return ap.parse_args()
 
 
@@ -256,6 +258,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     eng = jk.JK(mols)
     init_s = time.perf_counter() - t0
+    eng.set_option("use_graph", args.graph)
+    eng.set_option("branches", args.branches)
     Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
     Js = [torch.empty_like(d) for d in Ds]
     Ks = [torch.empty_like(d) for d in Ds]
@@ -391,6 +395,7 @@ def run_ours(args):
                        "natm_range": [min(m.natm for m in mols), max(m.natm for m in mols)],
                        "precision": args.precision, "cutoff": args.cutoff,
                        "l2": "flushed before every step (256 MiB write)",
+                       "graph": args.graph, "branches": args.branches,
                        "parallelism": f"{ws} independent batch(es), one per GPU"},
             "quartets_per_step": quartets / args.steps,
             "prim_quartets_per_step": sum(s["prim_quartets"] for s in stats) / args.steps,

@@ -164,7 +164,8 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * default 1e-7), "router_band" (K, default 100), "pair_cutoff" (shell pairs
  * with Q_ab at or below it are dropped at init, default 1e-18),
  * "use_graph" (0/1), "use_dmax" (0/1: 0 screens with Dmax := 1),
- * "profile" (0/1: CUDA events around every integral launch, see jk_profile),
+ * "profile" (0/1: CUDA events around every integral launch, see jk_profile;
+ * they become event nodes when the build is captured into a graph),
  * "branches" (1..8: class kernels forked over this many streams / graph
  * branches). With "use_graph" = 1 the first build of a flag combination is
  * captured into a CUDA graph on an internal stream and replayed on `stream`

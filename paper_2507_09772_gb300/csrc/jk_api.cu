@@ -483,7 +483,15 @@ struct Launch {
     int c1, c2;        // pair classes (bra, ket)
     KSpec spec[2];     // [0] FP64, [1] FP32
     double cost;       // scheduling estimate
+    long long *d_prefix = nullptr;  // nbra + 1 work-item offsets (chunks of kets per bra)
+    long long nitems = 0;
 };
+
+// Kets per work item. A bra pair's candidate kets (those whose Schwarz
+// product can exceed JK_ITEM_EPS with Dmax = 1) are split into chunks of this
+// size; the last chunk always runs to the molecule's last ket.
+#define JK_CHUNK 64
+#define JK_ITEM_EPS 1e-15
 
 }  // namespace
 
@@ -508,7 +516,7 @@ struct jk_handle {
     unsigned long long *d_dmax_mol = nullptr;
     double *d_rys64 = nullptr;
     float *d_rys32 = nullptr;
-    int *d_work = nullptr;                 // one counter per launch
+    unsigned long long *d_work = nullptr;  // one counter per launch
     unsigned long long *d_stats = nullptr; // two per launch
     int *d_err = nullptr;
     long long *d_tile_off = nullptr;
@@ -555,6 +563,7 @@ void free_handle(jk_handle *h)
 {
     if (!h) return;
     for (auto &c : h->classes) { cudaFree(c.d_beg); cudaFree(c.d_end); }
+    for (auto &L : h->launches) cudaFree(L.d_prefix);
     cudaFree(h->d_sh_mol); cudaFree(h->d_mol_sh0); cudaFree(h->d_sh_ao); cudaFree(h->d_sh_nc);
     cudaFree(h->d_pairs); cudaFree(h->d_pp64); cudaFree(h->d_pp32); cudaFree(h->d_mols);
     cudaFree(h->d_dmax); cudaFree(h->d_dmax_mol); cudaFree(h->d_rys64); cudaFree(h->d_rys32);
@@ -873,7 +882,32 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
                 s.fp32 = t;
                 choose_fragments(s, false);
             }
-            L.cost = (double)A.n * B.n * class_flops(L.spec[0], 1);
+            // work items: per bra, ceil(candidates / JK_CHUNK) (at least one), where the
+            // candidates are the kets (sorted by Q) with Q_ab Q_cd > JK_ITEM_EPS
+            std::vector<long long> pre(A.n + 1, 0);
+            double work = 0;
+            for (int m = 0; m < nmol; ++m) {
+                const int b0 = A.beg[m], b1 = A.end[m];
+                const int k0 = B.beg[m], k1 = B.end[m];
+                for (int bi = b0; bi < b1; ++bi) {
+                    const double qa = h->h_pairs[A.off + bi].Q;
+                    const int kfirst = (i == j) ? bi : k0;
+                    // kets with qa * Q_cd > eps form a prefix of [k0, k1)
+                    int lo = k0, hi = k1;
+                    while (lo < hi) {
+                        int mid = (lo + hi) / 2;
+                        if (qa * h->h_pairs[B.off + mid].Q > JK_ITEM_EPS) lo = mid + 1; else hi = mid;
+                    }
+                    long long ncand = std::max(0, lo - kfirst);
+                    long long nch = std::max(1LL, (ncand + JK_CHUNK - 1) / JK_CHUNK);
+                    pre[bi + 1] = nch;
+                    work += (double)ncand;
+                }
+            }
+            for (int bi = 0; bi < A.n; ++bi) pre[bi + 1] += pre[bi];
+            L.nitems = pre[A.n];
+            if ((rc = upload(&L.d_prefix, pre))) return rc;
+            L.cost = work * class_flops(L.spec[0], 1);
             h->launches.push_back(L);
         }
     std::stable_sort(h->launches.begin(), h->launches.end(), [](const Launch &x, const Launch &y) { return x.cost > y.cost; });
@@ -899,7 +933,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     CK(cudaMalloc(&h->d_dmax_mol, sizeof(unsigned long long) * nmol));
     CK(cudaMalloc(&h->d_mols, sizeof(JkMol) * nmol));
     const size_t nl = h->launches.size() * 2;
-    CK(cudaMalloc(&h->d_work, sizeof(int) * nl));
+    CK(cudaMalloc(&h->d_work, sizeof(unsigned long long) * nl));
     CK(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 3 * nl));
     CK(cudaMalloc(&h->d_err, sizeof(int)));
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
@@ -1053,7 +1087,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         h->prof_ev.resize(2 * specs.size());
         for (size_t e = have; e < h->prof_ev.size(); ++e) CK(cudaEventCreate(&h->prof_ev[e]));
     }
-    const int nbranch = prof ? 1 : std::max(1, std::min(h->branches, JK_MAX_BRANCHES + 1));
+    const int nbranch = std::max(1, std::min(h->branches, JK_MAX_BRANCHES + 1));
     int nlaunch_aux = 0;
 
     // Everything a build does on the device, in order, on stream s (and, for
@@ -1074,7 +1108,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             CK(cudaGetLastError());
             ++nlaunch_aux;
         }
-        CK(cudaMemsetAsync(h->d_work, 0, sizeof(int) * nl, s0));
+        CK(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long) * nl, s0));
         CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 3 * nl, s0));
         CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, s0));
         jk_dmax_kernel<<<h->nshell, 128, 0, s0>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
@@ -1128,14 +1162,16 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.log_n = h->d_logn;
             a.log_cap = logs ? logs->cap : 0;
             a.nbra = A.n;
+            a.item_prefix = L.d_prefix;
+            a.chunk = JK_CHUNK;
             a.same_class = (L.c1 == L.c2) ? 1 : 0;
             a.with_j = with_j ? 1 : 0;
             a.with_k = with_k ? 1 : 0;
             a.use_dmax = h->use_dmax;
             a.ndm = ndm;
             int grid = std::max(1, ki[k].blocks_per_sm) * h->num_sms;
-            const long long units = specs[k].G() <= 32 ? 4 : 1;   // bra pairs in flight per CTA
-            long long need = ((long long)A.n + units - 1) / units;
+            const long long units = specs[k].G() <= 32 ? 4 : 1;   // work items in flight per CTA
+            long long need = (L.nitems + units - 1) / units;
             if (need < grid) grid = (int)std::max(1LL, need);
             void *params[] = {&a};
             if (prof) CK(cudaEventRecord(h->prof_ev[2 * k], sk));
@@ -1167,13 +1203,13 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
     };
 
     if (logs) CK(cudaMemsetAsync(h->d_logn, 0, sizeof(unsigned long long), st));
-    if (h->use_graph && !prof && !logs) {
+    if (h->use_graph && !logs) {
         // one CUDA graph per flag combination, captured on the handle's own
         // stream and replayed on the caller's; per-call pointers live in the
         // device descriptors copied above, so the graph stays valid.
         char keyb[160];
-        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%d/%d/%zu", ndm, with_j, with_k, mode, cutoff, h->tau32,
-                 h->use_dmax, nbranch, h->cart_gen);
+        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d", ndm, with_j, with_k, mode, cutoff, h->tau32,
+                 h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0);
         std::string key = keyb;
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {

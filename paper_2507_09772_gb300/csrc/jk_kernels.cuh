@@ -551,6 +551,19 @@ __device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol 
                     atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, (double)jab[m][ia][ib]);
 }
 
+// Work item t -> bra pair i (binary search in the item prefix) and the ket
+// range of its chunk. The last chunk of a bra runs to the molecule's last
+// ket, so the partition covers every candidate whatever the estimate was.
+__device__ __forceinline__ int jk_item_bra(const JkClassArgs &args, long long t)
+{
+    int lo = 0, hi = args.nbra - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(args.item_prefix + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------- the class kernel
 // Persistent: warps (or, for groups of more than 32 threads, whole CTAs)
 // take bra pairs from a global counter until none are left.
@@ -578,15 +591,21 @@ jk_class_kernel(const JkClassArgs args)
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        const long long nitems = args.item_prefix[args.nbra];
         for (;;) {
-            int item = 0;
-            if (lane == 0) item = atomicAdd(args.work, 1);
-            item = __shfl_sync(0xffffffffu, item, 0);
-            if (item >= args.nbra) break;
+            long long t = 0;
+            if (lane == 0) t = (long long)atomicAdd(args.work, 1ull);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= nitems) break;
+            const int item = jk_item_bra(args, t);
+            const int ch = (int)(t - __ldg(args.item_prefix + item));
+            const int nch = (int)(__ldg(args.item_prefix + item + 1) - __ldg(args.item_prefix + item));
             const JkPair bra = args.bra[item];
             const JkMol mol = args.mols[bra.mol];
-            const int kb = args.same_class ? item : args.ket_beg[bra.mol];
-            const int ke = args.ket_end[bra.mol];
+            const int kb0 = args.same_class ? item : args.ket_beg[bra.mol];
+            const int kend = args.ket_end[bra.mol];
+            const int kb = min(kend, kb0 + ch * args.chunk);
+            const int ke = (ch == nch - 1) ? kend : min(kend, kb + args.chunk);
             const double *dmx = args.dmax + mol.dmax_off;
             const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
             const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
@@ -650,7 +669,7 @@ jk_class_kernel(const JkClassArgs args)
         }
     } else {
         // one group per CTA of round_up(G, 32) threads
-        __shared__ int s_item;
+        __shared__ long long s_item;
         __shared__ unsigned s_mask;
         __shared__ int s_stop;
         const int tg = threadIdx.x;
@@ -660,16 +679,22 @@ jk_class_kernel(const JkClassArgs args)
         R *grp = reinterpret_cast<R *>(jk_smem_raw);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        const long long nitems = args.item_prefix[args.nbra];
         for (;;) {
-            if (threadIdx.x == 0) s_item = atomicAdd(args.work, 1);
+            if (threadIdx.x == 0) s_item = (long long)atomicAdd(args.work, 1ull);
             __syncthreads();
-            const int item = s_item;
+            const long long t = s_item;
             __syncthreads();
-            if (item >= args.nbra) break;
+            if (t >= nitems) break;
+            const int item = jk_item_bra(args, t);
+            const int ch = (int)(t - __ldg(args.item_prefix + item));
+            const int nch = (int)(__ldg(args.item_prefix + item + 1) - __ldg(args.item_prefix + item));
             const JkPair bra = args.bra[item];
             const JkMol mol = args.mols[bra.mol];
-            const int kb = args.same_class ? item : args.ket_beg[bra.mol];
-            const int ke = args.ket_end[bra.mol];
+            const int kb0 = args.same_class ? item : args.ket_beg[bra.mol];
+            const int kend = args.ket_end[bra.mol];
+            const int kb = min(kend, kb0 + ch * args.chunk);
+            const int ke = (ch == nch - 1) ? kend : min(kend, kb + args.chunk);
             const double *dmx = args.dmax + mol.dmax_off;
             const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
             const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;

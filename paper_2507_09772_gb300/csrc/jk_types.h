@@ -61,7 +61,9 @@ struct JkClassArgs {
     const double *dmax_mol;      // per molecule: max over its table
     const double *rys64;         // FP64 Rys tables
     const float *rys32;          // FP32 Rys tables
-    int *work;                   // work counter (zeroed before the launch)
+    unsigned long long *work;    // work counter (zeroed before the launch)
+    const long long *item_prefix;  // nbra + 1: first work item of each bra pair
+    int chunk;                   // kets per work item (the last item of a bra runs to ket_end)
     unsigned long long *stats;   // [0] quartets, [1] primitive quartets, [2] routed band quartets
     int *err;                    // device error word
     double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi
