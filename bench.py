@@ -242,6 +242,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
+    from paper_2507_09772_gb300 import dist as jdist
     from paper_2507_09772_gb300 import jk, synth
 
     ws, rank, local = dist_env()
@@ -254,7 +255,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     jk.load_library()
-    mols = synth.batched_631gs(args.nmol, seed_base=1001 + rank * 1000)
+    mols = synth.batched_631gs(args.nmol, seed_base=jdist.batch_seed_base(rank))
     t0 = time.perf_counter()
     eng = jk.JK(mols)
     init_s = time.perf_counter() - t0
@@ -306,13 +307,11 @@ def run_ours(args):
     eng.set_option("profile", 0)
     quartets = sum(s["quartets_fp64"] + s["quartets_fp32"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    ms_t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    q_t = torch.tensor([float(quartets)], dtype=torch.float64, device="cuda")
     if pg:
-        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
-        pg.all_reduce(q_t, op=pg.ReduceOp.SUM)
-    ms_max = float(ms_t.item())
-    value = float(q_t.item()) / (ms_max * 1e-3)
+        ms_max, q_all = jdist.reduce_step_timing(pg, ms_total, quartets, device="cuda")
+    else:
+        ms_max, q_all = ms_total, float(quartets)
+    value = q_all / (ms_max * 1e-3)
 
     # dominant integral kernel and its roofline (FP64 or FP32 FMA pipe)
     total_kernel_ms = sum(v["ms"] for v in prof.values())
@@ -366,14 +365,13 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1)
-        t_e = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-        n_e = torch.tensor([float(nq)], dtype=torch.float64, device="cuda")
         if pg:
-            pg.all_reduce(t_e, op=pg.ReduceOp.MAX)
-            pg.all_reduce(n_e, op=pg.ReduceOp.SUM)
-        e2e = {"value": float(n_e.item()) / (float(t_e.item()) * 1e-3), "unit": UNIT,
+            t_e, n_e = jdist.reduce_step_timing(pg, ms_e2e, nq, device="cuda")
+        else:
+            t_e, n_e = ms_e2e, float(nq)
+        e2e = {"value": n_e / (t_e * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": float(t_e.item()) / args.steps}
+               "ms_per_step": t_e / args.steps}
 
     # the accelerated forms on the same inputs, against this FP64 build
     forms = None

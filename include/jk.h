@@ -166,6 +166,10 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * "use_graph" (0/1), "use_dmax" (0/1: 0 screens with Dmax := 1),
  * "profile" (0/1: CUDA events around every integral launch, see jk_profile;
  * they become event nodes when the build is captured into a graph),
+ * "part_count", "part_index" (a build computes only part part_index of
+ * part_count of every class kernel's work; J and K are then partial sums
+ * whose sum over the parts is the full result, i.e. one sum all-reduce
+ * combines GPUs that split one batch),
  * "branches" (1..8: class kernels forked over this many streams / graph
  * branches). With "use_graph" = 1 the first build of a flag combination is
  * captured into a CUDA graph on an internal stream and replayed on `stream`

@@ -471,6 +471,17 @@ double class_flops(const KSpec &s, int ndm)
     return P * prim + ndm * 2.0 * 6.0 * ne;
 }
 
+// Modelled FLOPs of nq contracted quartets of which np primitive quartets
+// were evaluated (the rest skipped by the primitive Schwarz screen).
+double flops_of(const KSpec &s, int ndm, unsigned long long nq, unsigned long long np)
+{
+    KSpec one = s;
+    one.na = one.nb = one.nc = one.nd = 1;
+    const double contract = ndm * 2.0 * 6.0 * ncart(s.la) * ncart(s.lb) * ncart(s.lc) * ncart(s.ld);
+    const double prim = class_flops(one, 0);
+    return (double)np * prim + (double)nq * contract;
+}
+
 // ------------------------------------------------------------ plan data
 struct PairClass {
     int la, lb, na, nb;
@@ -531,6 +542,8 @@ struct jk_handle {
     // options
     double tau32 = 1e-7, router_band = 100.0, pair_cutoff = 1e-18;
     int use_graph = 0, use_dmax = 1, profile = 0;
+    int part_index = 0, part_count = 1;    // partitioned builds (multi-GPU split of one batch)
+    double prim_eps_rel = 1e-3;            // primitive threshold relative to the cutoff
     double init_ms = 0, compile_ms = 0;
     std::vector<cudaEvent_t> prof_ev;      // two per launch slot
     std::vector<jk_launch_prof> prof;
@@ -796,6 +809,76 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     }
     std::vector<double> q(ncand);
     CK(cudaMemcpy(q.data(), d_q, sizeof(double) * ncand, cudaMemcpyDeviceToHost));
+
+    // ---- primitive-pair Schwarz factors: the Schwarz kernel of each pair
+    // class on single-primitive pseudo pairs (same centres, pp_off pointing
+    // at one primitive pair), then every shell pair's primitive pairs sorted
+    // by them, largest first
+    {
+        std::vector<JkPair> pseudo((size_t)npp);
+        std::vector<KSpec> specs;
+        std::vector<std::pair<long long, long long>> ranges;
+        long long i0 = 0;
+        while (i0 < ncand) {
+            long long i1 = i0;
+            while (i1 < ncand && cand[i1].cls == cand[i0].cls) ++i1;
+            for (long long i = i0; i < i1; ++i) {
+                const int n = shells[ca[i]].nprim * shells[cb[i]].nprim;
+                for (int k = 0; k < n; ++k) {
+                    JkPair pr = cp[i];
+                    pr.pp_off = cpp[i] + k;
+                    pseudo[cpp[i] + k] = pr;
+                }
+            }
+            const jk_shell &sa = shells[cand[i0].a], &sb = shells[cand[i0].b];
+            KSpec sp;
+            sp.kind = 1;
+            sp.la = sp.lc = sa.l; sp.lb = sp.ld = sb.l; sp.na = sp.nb = sp.nc = sp.nd = 1;
+            choose_fragments(sp, true);
+            specs.push_back(sp);
+            ranges.push_back({cpp[i0], i1 < ncand ? cpp[i1] : npp});
+            i0 = i1;
+        }
+        JkPair *d_pseudo = nullptr;
+        double *d_qp = nullptr;
+        int *d_cnt = nullptr;
+        JkPrimPair64 *n64 = nullptr;
+        JkPrimPair32 *n32 = nullptr;
+        auto cl2 = [&]() { cudaFree(d_pseudo); cudaFree(d_qp); cudaFree(d_cnt); cudaFree(n64); cudaFree(n32); };
+        struct G3 { std::function<void()> f; ~G3() { f(); } } g3{cl2};
+        if ((rc = upload(&d_pseudo, pseudo))) return rc;
+        CK(cudaMalloc(&d_qp, sizeof(double) * npp));
+        std::vector<KInfo> ki;
+        auto tc = std::chrono::steady_clock::now();
+        if ((rc = ensure_kernels(specs, ki))) return rc;
+        h->compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc).count();
+        for (size_t k = 0; k < specs.size(); ++k) {
+            JkSchwarzArgs a;
+            a.pairs = d_pseudo + ranges[k].first;
+            a.pp64 = h->d_pp64;
+            a.rys64 = h->d_rys64;
+            a.Qout = d_qp + ranges[k].first;
+            a.npair = (int)(ranges[k].second - ranges[k].first);
+            const long long groups = specs[k].groups_per_cta();
+            unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((a.npair + groups - 1) / groups,
+                                                                                (long long)h->num_sms * 8));
+            void *params[] = {&a};
+            CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem, 0,
+                                            params, nullptr);
+            if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "primitive Schwarz launch failed: %d", (int)r);
+        }
+        std::vector<int> cnt(ncand);
+        for (long long i = 0; i < ncand; ++i) cnt[i] = shells[ca[i]].nprim * shells[cb[i]].nprim;
+        if ((rc = upload(&d_cnt, cnt))) return rc;
+        CK(cudaMalloc(&n64, sizeof(JkPrimPair64) * npp));
+        CK(cudaMalloc(&n32, sizeof(JkPrimPair32) * npp));
+        jk_primsort_kernel<<<(unsigned)((ncand + 127) / 128), 128>>>((int)ncand, d_cpp, d_cnt, d_qp, h->d_pp64,
+                                                                      h->d_pp32, n64, n32);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+        std::swap(h->d_pp64, n64);
+        std::swap(h->d_pp32, n32);
+    }
 
     // ---- prune, group by (class, molecule), sort by Q descending
     std::vector<long long> order;
@@ -1163,7 +1246,10 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.log_cap = logs ? logs->cap : 0;
             a.nbra = A.n;
             a.item_prefix = L.d_prefix;
+            a.item_lo = L.nitems * h->part_index / h->part_count;
+            a.item_hi = L.nitems * (h->part_index + 1) / h->part_count;
             a.chunk = JK_CHUNK;
+            a.prim_eps = cutoff * h->prim_eps_rel;
             a.same_class = (L.c1 == L.c2) ? 1 : 0;
             a.with_j = with_j ? 1 : 0;
             a.with_k = with_k ? 1 : 0;
@@ -1171,14 +1257,15 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.ndm = ndm;
             int grid = std::max(1, ki[k].blocks_per_sm) * h->num_sms;
             const long long units = specs[k].G() <= 32 ? 4 : 1;   // work items in flight per CTA
-            long long need = (L.nitems + units - 1) / units;
+            long long need = (a.item_hi - a.item_lo + units - 1) / units;
             if (need < grid) grid = (int)std::max(1LL, need);
             void *params[] = {&a};
-            if (prof) CK(cudaEventRecord(h->prof_ev[2 * k], sk));
+            // External records become event nodes when captured into a graph
+            if (prof) CK(cudaEventRecordWithFlags(h->prof_ev[2 * k], sk, cudaEventRecordExternal));
             CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem,
                                             (CUstream)sk, params, nullptr);
             if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "launch of %s failed: %d", specs[k].name().c_str(), (int)r);
-            if (prof) CK(cudaEventRecord(h->prof_ev[2 * k + 1], sk));
+            if (prof) CK(cudaEventRecordWithFlags(h->prof_ev[2 * k + 1], sk, cudaEventRecordExternal));
         }
         if (nbranch > 1) {
             for (int b = 1; b < nbranch; ++b) {
@@ -1208,8 +1295,9 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         // stream and replayed on the caller's; per-call pointers live in the
         // device descriptors copied above, so the graph stays valid.
         char keyb[160];
-        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d", ndm, with_j, with_k, mode, cutoff, h->tau32,
-                 h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0);
+        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d/%d/%d/%a", ndm, with_j, with_k, mode, cutoff,
+                 h->tau32, h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0, h->part_index,
+                 h->part_count, h->prim_eps_rel);
         std::string key = keyb;
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
@@ -1252,7 +1340,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             else stats->quartets_fp32 += (int64_t)nq;
             if (tier[k] == 1 && mode == JK_PREC_MIXED_ROUTED) routed_fp32 += (int64_t)cnt[3 * slot + 2];
             stats->prim_quartets += (int64_t)np;
-            stats->flops_model += (double)nq * class_flops(specs[k], ndm);
+            stats->flops_model += flops_of(specs[k], ndm, nq, np);
             if (prof) {
                 jk_launch_prof p;
                 const KSpec &x = specs[k];
@@ -1267,7 +1355,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                 float lm = 0;
                 CK(cudaEventElapsedTime(&lm, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]));
                 p.ms = lm;
-                p.flops_model = (double)nq * class_flops(x, ndm);
+                p.flops_model = flops_of(x, ndm, nq, np);
                 h->prof.push_back(p);
             }
         }
@@ -1443,6 +1531,19 @@ int jk_set_option(jk_handle *h, const char *key, double value)
     else if (k == "use_graph") h->use_graph = value != 0;
     else if (k == "use_dmax") h->use_dmax = value != 0;
     else if (k == "profile") h->profile = value != 0;
+    else if (k == "prim_eps_rel") {
+        if (!(value >= 0 && value <= 1)) return fail(JK_ERR_ARG, "prim_eps_rel must be in [0, 1]");
+        h->prim_eps_rel = value;
+    }
+    else if (k == "part_count") {
+        if (!(value >= 1 && value <= 65536)) return fail(JK_ERR_ARG, "part_count must be in [1, 65536]");
+        h->part_count = (int)value;
+        if (h->part_index >= h->part_count) h->part_index = 0;
+    }
+    else if (k == "part_index") {
+        if (!(value >= 0 && value < h->part_count)) return fail(JK_ERR_ARG, "part_index must be in [0, part_count)");
+        h->part_index = (int)value;
+    }
     else if (k == "branches") {
         if (!(value >= 1 && value <= JK_MAX_BRANCHES + 1)) return fail(JK_ERR_ARG, "branches must be in [1, %d]", JK_MAX_BRANCHES + 1);
         h->branches = (int)value;
@@ -1462,6 +1563,9 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "use_dmax") *value = h->use_dmax;
     else if (k == "profile") *value = h->profile;
     else if (k == "branches") *value = h->branches;
+    else if (k == "part_count") *value = h->part_count;
+    else if (k == "prim_eps_rel") *value = h->prim_eps_rel;
+    else if (k == "part_index") *value = h->part_index;
     else if (k == "graphs") *value = (double)h->graphs.size();
     else if (k == "init_ms") *value = h->init_ms;
     else if (k == "compile_ms") *value = h->compile_ms;

@@ -52,7 +52,7 @@ __device__ __forceinline__ float jk_rsqrt(float x) { return rsqrtf(x); }
 // ----------------------------------------------------- Rys roots, weights
 // Root r and weight r of the N-point rule at T. The piecewise polynomials
 // cover 0 <= T < tmax; above it the half-range Gauss-Hermite limit
-// u = x^2 / T, w = w_h / sqrt(T) holds (evaluated in FP64 in both tiers).
+// u = x^2 / T, w = w_h / sqrt(T) holds (evaluated in the tier's precision).
 template <int N>
 __device__ __forceinline__ void jk_rys_one(double T, int r, const double *__restrict__ tab,
                                            double &u, double &w)
@@ -65,11 +65,17 @@ __device__ __forceinline__ void jk_rys_one(double T, int r, const double *__rest
     }
     int k = min((int)(T * RYS64_INVH), rys64_nint[N] - 1);
     double x = (T - k * RYS64_H) * (2.0 * RYS64_INVH) - 1.0;
-    const double *cu = tab + rys64_offset[N] + (long long)k * (2 * N * (RYS64_DEG + 1)) + r * (RYS64_DEG + 1);
-    const double *cw = cu + N * (RYS64_DEG + 1);
-    double au = __ldg(cu + RYS64_DEG), aw = __ldg(cw + RYS64_DEG);
+    // per function 8 doubles: c0..c5, then c6..c9 as floats (terms below
+    // 2e-7 of c0, summed in FP32 and added to the FP64 Horner head)
+    const double *cu = tab + rys64_offset[N] + (long long)k * (2 * N * 8) + r * 8;
+    const double *cw = cu + N * 8;
+    const float xf = (float)x;
+    const float4 tu = __ldg(reinterpret_cast<const float4 *>(cu + 6));
+    const float4 tw = __ldg(reinterpret_cast<const float4 *>(cw + 6));
+    double au = (double)fmaf(fmaf(fmaf(tu.w, xf, tu.z), xf, tu.y), xf, tu.x);
+    double aw = (double)fmaf(fmaf(fmaf(tw.w, xf, tw.z), xf, tw.y), xf, tw.x);
 #pragma unroll
-    for (int i = RYS64_DEG - 1; i >= 0; --i) {
+    for (int i = 5; i >= 0; --i) {
         au = fma(au, x, __ldg(cu + i));
         aw = fma(aw, x, __ldg(cw + i));
     }
@@ -82,10 +88,11 @@ __device__ __forceinline__ void jk_rys_one(float T, int r, const float *__restri
                                            float &u, float &w)
 {
     if (T >= (float)rys32_tmax[N]) {
-        double Td = T;
-        double s = rsqrt(Td);
-        u = (float)(rys_gh[rys_gh_offset[N - 1] + r] * (s * s));
-        w = (float)(rys_gh[rys_gh_offset[N - 1] + N + r] * s);
+        // u = x^2 / T, w = w_h / sqrt(T): no cancellation, so FP32 keeps
+        // ~2 ulp; the Gauss-Hermite constants themselves are FP64-derived
+        const float s = rsqrtf(T);
+        u = (float)rys_gh[rys_gh_offset[N - 1] + r] * (s * s);
+        w = (float)rys_gh[rys_gh_offset[N - 1] + N + r] * s;
         return;
     }
     int k = min((int)(T * (float)RYS32_INVH), rys32_nint[N] - 1);
@@ -241,7 +248,7 @@ __device__ __forceinline__ void jk_group_sync(unsigned gmask)
 // memory (G > 1), gmask the group's lane mask.
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
           int GA, int GB, int GC, int GD, typename R>
-__device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
+__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, double qthr,
                                            const typename JkPP<R>::T *__restrict__ pp,
                                            const R *__restrict__ rys, R *grp, unsigned gmask, int tg, bool act,
                                            const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD>> &off,
@@ -254,11 +261,18 @@ __device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
     const R CDx = (R)ket.ABx, CDy = (R)ket.ABy, CDz = (R)ket.ABz;
     const PPT *bpp = pp + bra.pp_off;
     const PPT *kpp = pp + ket.pp_off;
+    // primitive pairs are sorted by their Schwarz factor q (largest first):
+    // stop a loop at the first q_ij q_kl <= qthr (= prim_eps / Dmax)
+    const double qk0 = (double)kpp[0].q;
+    int nprim = 0;
 #pragma unroll 1
     for (int ij = 0; ij < NPA * NPB; ++ij) {
         const PPT bp = bpp[ij];
+        if ((double)bp.q * qk0 <= qthr) break;
         for (int kl = 0; kl < NPC * NPD; ++kl) {
             const PPT kp = kpp[kl];
+            if ((double)bp.q * (double)kp.q <= qthr) break;
+            ++nprim;
             const R p = bp.p, q = kp.p;
             const R rpq = jk_rsqrt(p + q);
             const R inv_pq = rpq * rpq;
@@ -347,6 +361,7 @@ __device__ __forceinline__ void jk_quartet(const JkPair &bra, const JkPair &ket,
             }
         }
     }
+    return nprim;
 }
 
 template <typename R> __device__ __forceinline__ const typename JkPP<R>::T *jk_pp(const JkClassArgs &a);
@@ -363,11 +378,12 @@ template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassA
 template <int MODE>
 __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkPairFeat &braf,
                                           const JkMol &mol, const double *dmx, double dmol, int j, int ke,
-                                          bool &sig, bool &stop, bool &band)
+                                          bool &sig, bool &stop, bool &band, double &dmq)
 {
     sig = false;
     stop = false;
     band = false;
+    dmq = 1.0;
     if (j >= ke) return;
     const double bq = bra.Q * args.ket[j].Q;
     if (bq * dmol <= args.lo) { stop = true; return; }
@@ -382,6 +398,7 @@ __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair 
             dm = fmax(dm, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
         }
     }
+    dmq = dm;
     const double B = bq * dm;
     sig = (B > args.lo) && (B <= args.hi);
     if (MODE == 1 && sig && B > args.tau && B <= args.band_hi) {
@@ -591,12 +608,11 @@ jk_class_kernel(const JkClassArgs args)
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
-        const long long nitems = args.item_prefix[args.nbra];
         for (;;) {
             long long t = 0;
-            if (lane == 0) t = (long long)atomicAdd(args.work, 1ull);
+            if (lane == 0) t = args.item_lo + (long long)atomicAdd(args.work, 1ull);
             t = __shfl_sync(0xffffffffu, t, 0);
-            if (t >= nitems) break;
+            if (t >= args.item_hi) break;
             const int item = jk_item_bra(args, t);
             const int ch = (int)(t - __ldg(args.item_prefix + item));
             const int nch = (int)(__ldg(args.item_prefix + item + 1) - __ldg(args.item_prefix + item));
@@ -618,10 +634,11 @@ jk_class_kernel(const JkClassArgs args)
                 for (int i = 0; i < FA; ++i)
 #pragma unroll
                     for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
-            unsigned long long nq = 0, nband = 0;
+            unsigned long long nq = 0, nband = 0, nprim = 0;
             for (int base = kb; base < ke; base += 32) {
                 bool sig, stop, band;
-                jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band);
+                double dmq;
+                jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq);
                 unsigned mask = __ballot_sync(0xffffffffu, sig);
                 nq += __popc(mask);
                 if (MODE == 1) nband += __popc(__ballot_sync(0xffffffffu, band));
@@ -634,12 +651,15 @@ jk_class_kernel(const JkClassArgs args)
                     }
 #pragma unroll 1
                     for (int q = 0; q < NGW && mask; ++q) mask &= mask - 1;
+                    const double dmk = __shfl_sync(0xffffffffu, dmq, myket >= 0 ? myket - base : 0);
                     if (myket >= 0) {
                         const JkPair ket = args.ket[myket];
                         R T[S::EPT];
 #pragma unroll
                         for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
-                        jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(bra, ket, pp, rys, grp, gmask, tg, true, off, T);
+                        const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(
+                            bra, ket, args.prim_eps / dmk, pp, rys, grp, gmask, tg, true, off, T);
+                        if (tg == 0) nprim += np;
                         R f = (R)1;
                         if (bra.a == bra.b) f *= (R)0.5;
                         if (ket.a == ket.b) f *= (R)0.5;
@@ -661,15 +681,17 @@ jk_class_kernel(const JkClassArgs args)
                 if (__any_sync(0xffffffffu, stop)) break;
             }
             if (DOJ && active) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+            for (int o = 16; o > 0; o >>= 1) nprim += __shfl_xor_sync(0xffffffffu, nprim, o);
             if (lane == 0 && nq) {
                 atomicAdd(args.stats, nq);
-                atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+                atomicAdd(args.stats + 1, nprim);
                 if (nband) atomicAdd(args.stats + 2, nband);
             }
         }
     } else {
         // one group per CTA of round_up(G, 32) threads
         __shared__ long long s_item;
+        __shared__ double s_dm[32];
         __shared__ unsigned s_mask;
         __shared__ int s_stop;
         const int tg = threadIdx.x;
@@ -679,13 +701,12 @@ jk_class_kernel(const JkClassArgs args)
         R *grp = reinterpret_cast<R *>(jk_smem_raw);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
-        const long long nitems = args.item_prefix[args.nbra];
         for (;;) {
-            if (threadIdx.x == 0) s_item = (long long)atomicAdd(args.work, 1ull);
+            if (threadIdx.x == 0) s_item = args.item_lo + (long long)atomicAdd(args.work, 1ull);
             __syncthreads();
             const long long t = s_item;
             __syncthreads();
-            if (t >= nitems) break;
+            if (t >= args.item_hi) break;
             const int item = jk_item_bra(args, t);
             const int ch = (int)(t - __ldg(args.item_prefix + item));
             const int nch = (int)(__ldg(args.item_prefix + item + 1) - __ldg(args.item_prefix + item));
@@ -707,11 +728,13 @@ jk_class_kernel(const JkClassArgs args)
                 for (int i = 0; i < FA; ++i)
 #pragma unroll
                     for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
-            unsigned long long nq = 0, nband = 0;
+            unsigned long long nq = 0, nband = 0, nprim = 0;
             for (int base = kb; base < ke; base += 32) {
                 if (threadIdx.x < 32) {
                     bool sig, stop, band;
-                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band);
+                    double dmq;
+                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq);
+                    s_dm[lane] = dmq;
                     const unsigned msk = __ballot_sync(0xffffffffu, sig);
                     const int anystop = __any_sync(0xffffffffu, stop);
                     const unsigned bmsk = __ballot_sync(0xffffffffu, band);
@@ -729,7 +752,9 @@ jk_class_kernel(const JkClassArgs args)
                     R T[S::EPT];
 #pragma unroll
                     for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
-                    jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(bra, ket, pp, rys, grp, 0u, tg, act, off, T);
+                    const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(
+                        bra, ket, args.prim_eps / s_dm[myket - base], pp, rys, grp, 0u, tg, act, off, T);
+                    nprim += np;
                     if (act) {
                         R f = (R)1;
                         if (bra.a == bra.b) f *= (R)0.5;
@@ -755,13 +780,17 @@ jk_class_kernel(const JkClassArgs args)
                         }
                         __syncthreads();
                     }
+                    // every thread has read s_dm for this quartet before warp 0
+                    // may screen the next chunk (a quartet can skip all its
+                    // primitives and so pass no barrier inside jk_quartet)
+                    __syncthreads();
                 }
                 if (stop) break;
             }
             if (DOJ && act) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
             if (threadIdx.x == 0 && nq) {
                 atomicAdd(args.stats, nq);
-                atomicAdd(args.stats + 1, nq * (unsigned long long)(NPA * NPB * NPC * NPD));
+                atomicAdd(args.stats + 1, nprim);
                 if (nband) atomicAdd(args.stats + 2, nband);
             }
         }
@@ -803,7 +832,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
                 double T[S::EPT];
 #pragma unroll
                 for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
+                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
                 if (ga == gc && gb == gd) {
 #pragma unroll
                     for (int ia = 0; ia < FA; ++ia)
@@ -831,7 +860,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
             double T[S::EPT];
 #pragma unroll
             for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
+            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
             double mx = 0.0;
             if (act && ga == gc && gb == gd) {
 #pragma unroll

@@ -24,15 +24,19 @@ struct JkPair {
 //   PA   = P - A
 //   K    = c_i c_j exp(-alpha beta |A-B|^2 / p) / p
 //   inv2p = 1 / (2 p)
+//   q    = primitive Schwarz factor sqrt(max |(ij|ij)|) (coefficients
+//          included); a shell pair's primitive pairs are sorted by q,
+//          largest first, so primitive loops can stop at the first
+//          q_ij q_kl Dmax at or below the primitive threshold
 struct JkPrimPair64 {
     double Px, Py, Pz, p;
     double PAx, PAy, PAz, K;
-    double inv2p, pad0, pad1, pad2;
+    double inv2p, q, pad1, pad2;
 };
 struct JkPrimPair32 {
     float Px, Py, Pz, p;
     float PAx, PAy, PAz, K;
-    float inv2p, pad0, pad1, pad2;
+    float inv2p, q, pad1, pad2;
 };
 
 // Per molecule of a handle.
@@ -63,7 +67,9 @@ struct JkClassArgs {
     const float *rys32;          // FP32 Rys tables
     unsigned long long *work;    // work counter (zeroed before the launch)
     const long long *item_prefix;  // nbra + 1: first work item of each bra pair
+    long long item_lo, item_hi;  // this build's share of the items [lo, hi) (partitioned builds)
     int chunk;                   // kets per work item (the last item of a bra runs to ket_end)
+    double prim_eps;             // skip primitive quartets with q_ij q_kl Dmax <= prim_eps
     unsigned long long *stats;   // [0] quartets, [1] primitive quartets, [2] routed band quartets
     int *err;                    // device error word
     double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi

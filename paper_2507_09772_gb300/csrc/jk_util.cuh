@@ -35,12 +35,13 @@ __global__ void jk_pairdata_kernel(int npair, const int *__restrict__ pa, const 
             r.PAz = r.Pz - A[2];
             r.K = ca * cb * exp(-al * be * ip * r2) * ip;
             r.inv2p = 0.5 * ip;
-            r.pad0 = r.pad1 = r.pad2 = 0.0;
+            r.q = 0.0;
+            r.pad1 = r.pad2 = 0.0;
             out64[o] = r;
             JkPrimPair32 s;
             s.Px = (float)r.Px; s.Py = (float)r.Py; s.Pz = (float)r.Pz; s.p = (float)p;
             s.PAx = (float)r.PAx; s.PAy = (float)r.PAy; s.PAz = (float)r.PAz; s.K = (float)r.K;
-            s.inv2p = (float)r.inv2p; s.pad0 = s.pad1 = s.pad2 = 0.f;
+            s.inv2p = (float)r.inv2p; s.q = 0.f; s.pad1 = s.pad2 = 0.f;
             out32[o] = s;
         }
     }
@@ -218,5 +219,32 @@ __global__ void jk_sph_kernel(const JkSphMol *__restrict__ mols, const int *__re
                     Dst[(long long)(sh_aos[a] + m) * M.nao_s + sh_aos[b] + n] = s;
                 }
         }
+    }
+}
+
+// Primitive Schwarz factors into the pair records, then each shell pair's
+// primitive pairs reordered by q (largest first), one thread per shell pair.
+__global__ void jk_primsort_kernel(int npair, const int *__restrict__ pp_off, const int *__restrict__ pp_cnt,
+                                   const double *__restrict__ qprim, const JkPrimPair64 *__restrict__ in64,
+                                   const JkPrimPair32 *__restrict__ in32, JkPrimPair64 *__restrict__ out64,
+                                   JkPrimPair32 *__restrict__ out32)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npair) return;
+    const int o = pp_off[t], n = pp_cnt[t];
+    for (int k = 0; k < n; ++k) {
+        // rank of record k: how many records precede it (q descending, ties by index)
+        const double qk = qprim[o + k];
+        int rank = 0;
+        for (int m = 0; m < n; ++m) {
+            const double qm = qprim[o + m];
+            if (qm > qk || (qm == qk && m < k)) ++rank;
+        }
+        JkPrimPair64 r = in64[o + k];
+        JkPrimPair32 s = in32[o + k];
+        r.q = qk;
+        s.q = (float)qk;
+        out64[o + rank] = r;
+        out32[o + rank] = s;
     }
 }

@@ -149,6 +149,55 @@ def evaluate(table: np.ndarray, params: dict, T: float):
     return acc[:N], acc[N:]
 
 
+SPLIT = 6   # FP64 tier: coefficients 0..SPLIT-1 in FP64, the rest as an FP32 tail
+
+
+def pack_split(table: np.ndarray, params: list):
+    """FP64-tier layout used by the kernels: per function 8 doubles (64 B):
+    c0..c5 as doubles, then c6..c9 as four floats in the last 16 bytes. The
+    tail terms are below 2e-7 of c0 on every interval, so summing them in
+    FP32 costs about 1e-14 relative while saving FP64 multiply-adds."""
+    deg = params[0]["deg"]
+    assert deg + 1 == SPLIT + 4
+    chunks = []
+    for p in params:
+        N = p["N"]
+        c = table[p["offset"]:p["offset"] + p["nint"] * 2 * N * (deg + 1)].reshape(-1, deg + 1)
+        out = np.zeros((c.shape[0], 8), dtype=np.float64)
+        out[:, :SPLIT] = c[:, :SPLIT]
+        tail = c[:, SPLIT:].astype(np.float32)
+        out[:, SPLIT:] = tail.view(np.float64).reshape(-1, 2)
+        chunks.append(out.ravel())
+    return np.concatenate(chunks)
+
+
+def evaluate_split(packed: np.ndarray, params: list, N: int, T: float):
+    """Host model of the kernel's split evaluation (FP32 tail, FP64 head)."""
+    p = params[N - 1]
+    if T >= p["tmax"]:
+        return evaluate(None, p, T)
+    offs = [0]
+    for q in params:
+        offs.append(offs[-1] + q["nint"] * 2 * q["N"] * 8)
+    h = p["h"]
+    k = int(T / h)
+    x = 2.0 * (T - k * h) / h - 1.0
+    base = offs[N - 1] + k * 2 * N * 8
+    blk = packed[base:base + 2 * N * 8].reshape(2 * N, 8)
+    xf = np.float32(x)
+    res = np.empty(2 * N)
+    for j in range(2 * N):
+        t = blk[j, SPLIT:].view(np.float32)
+        a = np.float32(t[3])
+        for i in (2, 1, 0):
+            a = np.float32(np.float32(a * xf) + t[i])
+        acc = float(a)
+        for i in range(SPLIT - 1, -1, -1):
+            acc = acc * x + blk[j, i]
+        res[j] = acc
+    return res[:N], res[N:]
+
+
 def _fmt(v: float) -> str:
     return float(v).hex()
 
@@ -160,10 +209,11 @@ def write_sources(outdir: str) -> dict:
     t32, p32 = fit_tables(FP32_FIT)
     with open(os.path.join(outdir, "rys_tables.inc.tmp"), "w") as f:
         f.write("// generated by rys_gen.py: Rys root/weight interpolation tables\n")
-        f.write(f"static const size_t rys_table64_size = {t64.size};\n")
+        t64p = pack_split(t64, p64)
+        f.write(f"static const size_t rys_table64_size = {t64p.size};\n")
         f.write("static const double rys_table64[] = {\n")
-        for i in range(0, t64.size, 4):
-            f.write(",".join(_fmt(v) for v in t64[i:i + 4]) + ",\n")
+        for i in range(0, t64p.size, 4):
+            f.write(",".join(_fmt(v) for v in t64p[i:i + 4]) + ",\n")
         f.write("};\n")
         f.write(f"static const size_t rys_table32_size = {t32.size};\n")
         f.write("static const double rys_table32_src[] = {\n")
@@ -175,9 +225,14 @@ def write_sources(outdir: str) -> dict:
         f.write("// generated by rys_gen.py: Rys table geometry and Gauss-Hermite limits\n")
         f.write("#pragma once\n")
         f.write(f"#define RYS_NMAX {NMAX}\n")
+        offs64, o = [], 0
+        for p in p64:
+            offs64.append(o)
+            o += p["nint"] * 2 * p["N"] * 8
         for tag, ps in (("64", p64), ("32", p32)):
+            offs = offs64 if tag == "64" else [p['offset'] for p in ps]
             f.write(f"__device__ __constant__ int rys{tag}_offset[{NMAX + 1}] = {{0,"
-                    + ",".join(str(p['offset']) for p in ps) + "};\n")
+                    + ",".join(str(x) for x in offs) + "};\n")
             f.write(f"#define RYS{tag}_DEG {ps[0]['deg']}\n")
             f.write(f"#define RYS{tag}_H {ps[0]['h']!r}\n")
             f.write(f"#define RYS{tag}_INVH {1.0 / ps[0]['h']!r}\n")

@@ -275,3 +275,44 @@ def test_graph_replay_and_branches_match_eager(branches):
     for a, b, c in zip(K0, K1, K2):
         assert float((a - b).abs().max()) <= 1e-12 and float((a - c).abs().max()) <= 1e-12
     assert s0["quartets_fp64"] == s1["quartets_fp64"] == s2["quartets_fp64"]
+
+
+def test_partitioned_builds_sum_to_the_full_build():
+    mols = [synth.batched_molecule(8, natm=12), synth.tiny_631gs()]
+    eng = jk.JK(mols)
+    Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
+    J0, K0, s0 = eng.build(Ds, stats=True)
+    Js = [torch.zeros_like(d) for d in Ds]
+    Ks = [torch.zeros_like(d) for d in Ds]
+    nq = 0
+    eng.set_option("part_count", 3)
+    for p in range(3):
+        eng.set_option("part_index", p)
+        J, K, st = eng.build(Ds, stats=True)
+        nq += st["quartets_fp64"]
+        for a, b in zip(Js, J):
+            a += b
+        for a, b in zip(Ks, K):
+            a += b
+    torch.cuda.synchronize()
+    eng.close()
+    assert nq == s0["quartets_fp64"]
+    for a, b in zip(Js, J0):
+        assert float((a - b).abs().max()) <= 1e-12
+    for a, b in zip(Ks, K0):
+        assert float((a - b).abs().max()) <= 1e-12
+
+
+def test_primitive_screening_changes_nothing_beyond_its_threshold():
+    mol = synth.batched_molecule(9, natm=14)
+    eng = jk.JK(mol)
+    D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+    J1, K1, s1 = eng.build(D, stats=True)                 # default: prim_eps = 1e-3 * cutoff
+    eng.set_option("prim_eps_rel", 0.0)
+    J0, K0, s0 = eng.build(D, stats=True)                 # every primitive quartet
+    torch.cuda.synchronize()
+    eng.close()
+    assert s1["quartets_fp64"] == s0["quartets_fp64"]
+    assert s1["prim_quartets"] < s0["prim_quartets"]
+    assert float((J1 - J0).abs().max()) <= 1e-12
+    assert float((K1 - K0).abs().max()) <= 1e-12

@@ -78,3 +78,16 @@ def test_fp32_tables_are_accurate_to_single_precision():
             u, W = rys_gen.evaluate(tab, params[N - 1], T)
             assert np.max(np.abs(u / ue - 1)) < 2e-6
             assert np.max(np.abs(W / We - 1)) < 2e-6
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 7])
+def test_split_precision_evaluation_matches_exact_rule(tables, N):
+    """The FP64 tier's layout: FP64 head c0..c5, FP32 tail c6..c9."""
+    tab, params = tables
+    packed = rys_gen.pack_split(tab, params)
+    rng = np.random.default_rng(10 + N)
+    for T in np.concatenate([rng.uniform(0, params[N - 1]["tmax"], 60), [0.0, 1e-7]]):
+        ue, We = rys_gen.rys_exact(N, T)
+        u, W = rys_gen.evaluate_split(packed, params, N, T)
+        assert np.max(np.abs(u / ue - 1)) < 6e-14
+        assert np.max(np.abs(W / We - 1)) < 6e-14
