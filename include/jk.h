@@ -166,6 +166,11 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * "use_graph" (0/1), "use_dmax" (0/1: 0 screens with Dmax := 1),
  * "profile" (0/1: CUDA events around every integral launch, see jk_profile;
  * they become event nodes when the build is captured into a graph),
+ * "omega" (range separation, Table 1 rys_type of the paper: 0 the Coulomb
+ * operator 1/r; w > 0 the long-range erf(w r)/r; w < 0 the short-range
+ * erfc(|w| r)/r; the Schwarz factors of 1/r bound both),
+ * "prim_eps" (primitive quartets with q_ij q_kl Dmax <= min(prim_eps,
+ * cutoff) are skipped; q is the primitive-pair Schwarz factor; default 1e-16),
  * "part_count", "part_index" (a build computes only part part_index of
  * part_count of every class kernel's work; J and K are then partial sums
  * whose sum over the parts is the full result, i.e. one sum all-reduce
@@ -248,13 +253,13 @@ int jk_measure_peak(int32_t which, double ms, double *flops_per_s);
 
 /* Ahead-of-time compilation of one class kernel (angular momenta la..ld,
  * primitive counts na..nd, n_dm, flags, fp32 = 1 for the FP32 tier, mode 0
- * plain / 1 routed / 2 router-label logging) into
+ * plain / 1 routed / 2 router-label logging, op 0 1/r / 1 erf / 2 erfc) into
  * the on-disk kernel cache (JK_KERNEL_CACHE, else next to the library).
  * Needs no GPU. *threads_per_quartet receives the fragmentation chosen.
  * JK_ERR_COMPILE with the NVRTC log in jk_last_error() on failure. */
 int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na, int32_t nb, int32_t nc,
                      int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32, int32_t mode,
-                     int32_t *threads_per_quartet, double *compile_ms);
+                     int32_t op, int32_t *threads_per_quartet, double *compile_ms);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *jk_last_error(void);

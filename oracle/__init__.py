@@ -81,8 +81,30 @@ def _load():
                                        _ip, ctypes.c_int, _dp, _ip, ctypes.c_int, _dp]
         lib.oracle_jk_rows.restype = ctypes.c_longlong
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_omega.argtypes = [ctypes.c_double]
+        lib.oracle_set_omega.restype = None
         _lib = lib
         return lib
+
+
+class omega_operator:
+    """Context: integrals of erf(w r)/r (w > 0), erfc(|w| r)/r (w < 0) or 1/r (w = 0).
+
+    The Schwarz factors stay those of 1/r (a valid bound for both attenuated
+    operators, whose Fourier transforms lie between 0 and that of 1/r)."""
+
+    def __init__(self, omega: float):
+        self.omega = float(omega)
+
+    def __enter__(self):
+        _load().oracle_set_omega(self.omega)
+        _current_omega[0] = self.omega
+        return self
+
+    def __exit__(self, *exc):
+        _load().oracle_set_omega(0.0)
+        _current_omega[0] = 0.0
+        return False
 
 
 def num_threads() -> int:
@@ -160,6 +182,21 @@ def schwarz(mol) -> np.ndarray:
     Q = np.zeros(nsh * nsh)
     _load().oracle_schwarz(sh, nsh, xyz, ex, co, Q)
     return Q.reshape(nsh, nsh)
+
+
+def schwarz_coulomb(mol) -> np.ndarray:
+    """Schwarz factors of the plain 1/r operator, whatever omega is set."""
+    lib = _load()
+    sh, nsh, xyz, ex, co = _basis_args(mol)
+    Q = np.zeros(nsh * nsh)
+    # the omega setting is module state of the C library; save, clear, restore
+    lib.oracle_set_omega(0.0)
+    lib.oracle_schwarz(sh, nsh, xyz, ex, co, Q)
+    lib.oracle_set_omega(_current_omega[0])
+    return Q.reshape(nsh, nsh)
+
+
+_current_omega = [0.0]
 
 
 def dmax(mol, Dcart) -> np.ndarray:
@@ -297,7 +334,7 @@ def jk(mol, D=None, cutoff: float = 1e-13, with_j=True, with_k=True, use_dmax=Tr
     ndm, nao = Dc.shape[0], Dc.shape[1]
     sh, nsh, xyz, ex, co = _basis_args(mol)
     if Q is None:
-        Q = schwarz(mol)
+        Q = schwarz_coulomb(mol)
     Dm = dmax(mol, Dc)
     J = np.zeros(ndm * nao * nao)
     K = np.zeros(ndm * nao * nao)
@@ -324,7 +361,7 @@ def jk_blocks(mol, jblocks, kblocks, D=None, cutoff: float = 1e-13, with_j=True,
     ndm, nao = Dc.shape[0], Dc.shape[1]
     sh, nsh, xyz, ex, co = _basis_args(mol)
     if Q is None:
-        Q = schwarz(mol)
+        Q = schwarz_coulomb(mol)
     Dm = dmax(mol, Dc)
     jb = np.ascontiguousarray(np.asarray(jblocks, dtype=np.int32).reshape(-1, 2))
     kb = np.ascontiguousarray(np.asarray(kblocks, dtype=np.int32).reshape(-1, 2))

@@ -168,10 +168,39 @@ static void hermite_R(int L, double rho, double X, double Y, double Z, double *R
 /* Unnormalised primitives with coefficient 1:
  *   out[((ia*nb + ib)*nc + ic)*nd + id] = (a_ia b_ib | c_ic d_id)
  * where a_ia = (x-Ax)^lx (y-Ay)^ly (z-Az)^lz exp(-alpha |r-A|^2). */
+/* Range separation of the Coulomb operator (Table 1 of the paper, rys_type):
+ * g_omega == 0: 1/r; g_omega > 0: erf(omega r)/r (long range);
+ * g_omega < 0: erfc(|omega| r)/r = 1/r - erf(|omega| r)/r (short range).
+ * For erf(omega r)/r the McMurchie-Davidson formula keeps its form with rho
+ * replaced by rho theta, theta = omega^2/(omega^2 + rho), and the prefactor
+ * multiplied by sqrt(theta). Set through oracle_set_omega. */
+static double g_omega = 0.0;
+void oracle_set_omega(double omega) { g_omega = omega; }
+
+static void eri_prim_block_op(int la, int lb, int lc, int ld,
+                              double aa, double ab, double ac, double ad,
+                              const double *A, const double *B, const double *C, const double *D,
+                              double scale, double omega, double *out, double *Rbuf);
+
 static void eri_prim_block(int la, int lb, int lc, int ld,
                            double aa, double ab, double ac, double ad,
                            const double *A, const double *B, const double *C, const double *D,
                            double scale, double *out, double *Rbuf)
+{
+    if (g_omega == 0.0) {
+        eri_prim_block_op(la, lb, lc, ld, aa, ab, ac, ad, A, B, C, D, scale, 0.0, out, Rbuf);
+    } else if (g_omega > 0.0) {
+        eri_prim_block_op(la, lb, lc, ld, aa, ab, ac, ad, A, B, C, D, scale, g_omega, out, Rbuf);
+    } else {
+        eri_prim_block_op(la, lb, lc, ld, aa, ab, ac, ad, A, B, C, D, scale, 0.0, out, Rbuf);
+        eri_prim_block_op(la, lb, lc, ld, aa, ab, ac, ad, A, B, C, D, -scale, -g_omega, out, Rbuf);
+    }
+}
+
+static void eri_prim_block_op(int la, int lb, int lc, int ld,
+                              double aa, double ab, double ac, double ad,
+                              const double *A, const double *B, const double *C, const double *D,
+                              double scale, double omega, double *out, double *Rbuf)
 {
     Etab Eab[3], Ecd[3];
     double p = aa + ab, q = ac + ad;
@@ -183,9 +212,10 @@ static void eri_prim_block(int la, int lb, int lc, int ld,
         Q[k] = (ac * C[k] + ad * D[k]) / q;
     }
     double rho = p * q / (p + q);
+    double theta = omega > 0.0 ? omega * omega / (omega * omega + rho) : 1.0;
     int L = la + lb + lc + ld;
-    hermite_R(L, rho, P[0] - Q[0], P[1] - Q[1], P[2] - Q[2], Rbuf);
-    double pref = scale * 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
+    hermite_R(L, rho * theta, P[0] - Q[0], P[1] - Q[1], P[2] - Q[2], Rbuf);
+    double pref = scale * sqrt(theta) * 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));
     int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
 #define R0(t, u, v) Rbuf[(((0) * RD + (t)) * RD + (u)) * RD + (v)]
     for (int ia = 0; ia < na; ++ia) {

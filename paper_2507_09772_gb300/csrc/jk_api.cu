@@ -106,6 +106,7 @@ struct KSpec {
     int ga = 1, gb = 1, gc = 1, gd = 1;
     int ndm = 1, doj = 1, dok = 1, fp32 = 0;
     int mode = 0;  // 0 plain, 1 routed (learned router in the band), 2 label logging
+    int op = 0;    // 0 1/r, 1 erf(w r)/r, 2 erfc(w r)/r
 
     std::string name() const
     {
@@ -113,12 +114,12 @@ struct KSpec {
         if (kind == 1)
             snprintf(b, sizeof b, "jk_schwarz_kernel<%d,%d,%d,%d,%d,%d,%d,%d>", la, lb, na, nb, ga, gb, gc, gd);
         else
-            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s,%d>", la, lb, lc,
-                     ld, na, nb, nc, nd, ga, gb, gc, gd, ndm, doj, dok, fp32 ? "float" : "double", mode);
+            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s,%d,%d>", la, lb,
+                     lc, ld, na, nb, nc, nd, ga, gb, gc, gd, ndm, doj, dok, fp32 ? "float" : "double", mode, op);
         return b;
     }
     int G() const { return ga * gb * gc * gd; }
-    int nr() const { return (la + lb + lc + ld) / 2 + 1; }
+    int nr() const { return ((la + lb + lc + ld) / 2 + 1) * (op == 2 ? 2 : 1); }
     int ni() const { return (la + 1) * (lb + 1) * (lc + 1) * (ld + 1); }
     int smem_group_reals() const { return G() == 1 ? 0 : nr() * 3 * ni() + 2 * nr(); }
     // G <= 32: four warps, each holding 32/G groups; G > 32: one group per CTA
@@ -432,7 +433,7 @@ void choose_fragments(KSpec &s, bool symmetric)
     const int nf[4] = {ncart(s.la), ncart(s.lb), ncart(s.lc), ncart(s.ld)};
     const int ne = nf[0] * nf[1] * nf[2] * nf[3];
     const int ni = s.ni();
-    const int reg_cap = s.fp32 ? 96 : 48;     // per-thread fragment budget (reals)
+    const int reg_cap = 48;                   // per-thread fragment budget (reals)
     const int gmax = symmetric ? 1024 : 256;  // threads per quartet (one CTA at most)
     const int g1_cap = s.fp32 ? 128 : 64;     // register-mode budget: fragment + 3 tables
     if (ne + 3 * ni <= g1_cap) { s.ga = s.gb = s.gc = s.gd = 1; return; }
@@ -543,7 +544,8 @@ struct jk_handle {
     double tau32 = 1e-7, router_band = 100.0, pair_cutoff = 1e-18;
     int use_graph = 0, use_dmax = 1, profile = 0;
     int part_index = 0, part_count = 1;    // partitioned builds (multi-GPU split of one batch)
-    double prim_eps_rel = 1e-3;            // primitive threshold relative to the cutoff
+    double prim_eps = 1e-16;               // primitive threshold (never above the cutoff)
+    double omega = 0.0;                    // range separation: 0 1/r, > 0 erf, < 0 erfc
     double init_ms = 0, compile_ms = 0;
     std::vector<cudaEvent_t> prof_ev;      // two per launch slot
     std::vector<jk_launch_prof> prof;
@@ -1094,6 +1096,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             KSpec s = h->launches[i].spec[t];
             s.ndm = ndm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0;
             s.mode = logs ? 2 : (mode == JK_PREC_MIXED_ROUTED ? 1 : 0);
+            s.op = h->omega == 0.0 ? 0 : (h->omega > 0.0 ? 1 : 2);
             specs.push_back(s);
             lidx.push_back((int)i);
             tier.push_back(t);
@@ -1249,7 +1252,8 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.item_lo = L.nitems * h->part_index / h->part_count;
             a.item_hi = L.nitems * (h->part_index + 1) / h->part_count;
             a.chunk = JK_CHUNK;
-            a.prim_eps = cutoff * h->prim_eps_rel;
+            a.prim_eps = std::min(cutoff, h->prim_eps);
+            a.omega = std::fabs(h->omega);
             a.same_class = (L.c1 == L.c2) ? 1 : 0;
             a.with_j = with_j ? 1 : 0;
             a.with_k = with_k ? 1 : 0;
@@ -1297,8 +1301,11 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         char keyb[160];
         snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d/%d/%d/%a", ndm, with_j, with_k, mode, cutoff,
                  h->tau32, h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0, h->part_index,
-                 h->part_count, h->prim_eps_rel);
+                 h->part_count, h->prim_eps);
         std::string key = keyb;
+        char ob[40];
+        snprintf(ob, sizeof ob, "/%a", h->omega);
+        key += ob;
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
@@ -1531,9 +1538,13 @@ int jk_set_option(jk_handle *h, const char *key, double value)
     else if (k == "use_graph") h->use_graph = value != 0;
     else if (k == "use_dmax") h->use_dmax = value != 0;
     else if (k == "profile") h->profile = value != 0;
-    else if (k == "prim_eps_rel") {
-        if (!(value >= 0 && value <= 1)) return fail(JK_ERR_ARG, "prim_eps_rel must be in [0, 1]");
-        h->prim_eps_rel = value;
+    else if (k == "omega") {
+        if (!std::isfinite(value)) return fail(JK_ERR_ARG, "omega must be finite");
+        h->omega = value;
+    }
+    else if (k == "prim_eps") {
+        if (!(value >= 0) || !std::isfinite(value)) return fail(JK_ERR_ARG, "prim_eps must be finite and >= 0");
+        h->prim_eps = value;
     }
     else if (k == "part_count") {
         if (!(value >= 1 && value <= 65536)) return fail(JK_ERR_ARG, "part_count must be in [1, 65536]");
@@ -1564,7 +1575,8 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "profile") *value = h->profile;
     else if (k == "branches") *value = h->branches;
     else if (k == "part_count") *value = h->part_count;
-    else if (k == "prim_eps_rel") *value = h->prim_eps_rel;
+    else if (k == "prim_eps") *value = h->prim_eps;
+    else if (k == "omega") *value = h->omega;
     else if (k == "part_index") *value = h->part_index;
     else if (k == "graphs") *value = (double)h->graphs.size();
     else if (k == "init_ms") *value = h->init_ms;
@@ -1830,7 +1842,7 @@ int jk_measure_peak(int32_t which, double ms, double *flops_per_s)
 
 int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na, int32_t nb, int32_t nc,
                      int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32, int32_t mode,
-                     int32_t *threads_per_quartet, double *compile_ms)
+                     int32_t op, int32_t *threads_per_quartet, double *compile_ms)
 {
     if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > JK_LMAX || lb > JK_LMAX || lc > JK_LMAX || ld > JK_LMAX)
         return fail(JK_ERR_UNSUPPORTED, "angular momentum out of range");
@@ -1839,11 +1851,13 @@ int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na,
         return fail(JK_ERR_UNSUPPORTED, "primitive count out of range");
     if (n_dm < 1 || n_dm > JK_NDM_MAX || (!with_j && !with_k)) return fail(JK_ERR_ARG, "bad n_dm or flags");
     if (mode < 0 || mode > 2 || (mode == 2 && fp32)) return fail(JK_ERR_ARG, "bad mode");
+    if (op < 0 || op > 2) return fail(JK_ERR_ARG, "bad op");
     KSpec s;
     s.kind = 0;
     s.la = la; s.lb = lb; s.lc = lc; s.ld = ld; s.na = na; s.nb = nb; s.nc = nc; s.nd = nd;
     s.ndm = n_dm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0; s.fp32 = fp32 ? 1 : 0;
     s.mode = mode;
+    s.op = op;
     choose_fragments(s, false);
     if (threads_per_quartet) *threads_per_quartet = s.G();
     try {

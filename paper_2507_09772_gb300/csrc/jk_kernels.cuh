@@ -169,7 +169,10 @@ __device__ __forceinline__ void jk_build_2d(R c00, R c00p, R b10, R b01, R b00, 
 }
 
 // ----------------------------------------------------------- class shape
-template <int LA, int LB, int LC, int LD, int GA, int GB, int GC, int GD>
+// OP: 0 the Coulomb operator 1/r; 1 erf(w r)/r (long range); 2 erfc(w r)/r
+// (short range) = 1/r minus the long-range part, i.e. a second root set with
+// negative weights (the range separation of Table 1, rys_type).
+template <int LA, int LB, int LC, int LD, int GA, int GB, int GC, int GD, int OP = 0>
 struct JkShape {
     static constexpr int NFA = jk_ncart(LA), NFB = jk_ncart(LB), NFC = jk_ncart(LC), NFD = jk_ncart(LD);
     static constexpr int FA = NFA / GA, FB = NFB / GB, FC = NFC / GC, FD = NFD / GD;
@@ -177,10 +180,11 @@ struct JkShape {
     static constexpr int EPT = FA * FB * FC * FD;
     static constexpr int L = LA + LB + LC + LD;
     static constexpr int NR = L / 2 + 1;
+    static constexpr int NRE = (OP == 2 ? 2 : 1) * NR;   // roots of all sets
     static constexpr int SD = 1, SC = LD + 1, SB = (LC + 1) * (LD + 1), SA = (LB + 1) * SB;
     static constexpr int NI = (LA + 1) * SA;
     // reals of shared memory per group (G > 1): 2D tables and the roots
-    static constexpr int SMEM_GROUP = (G == 1) ? 0 : (NR * 3 * NI + 2 * NR);
+    static constexpr int SMEM_GROUP = (G == 1) ? 0 : (NRE * 3 * NI + 2 * NRE);
     static_assert(NFA % GA == 0 && NFB % GB == 0 && NFC % GC == 0 && NFD % GD == 0, "fragment");
     static_assert(G <= 1024, "a group fits one CTA");
 };
@@ -191,11 +195,9 @@ struct JkOffsets {
     int a[3][S::FA], b[3][S::FB], c[3][S::FC], d[3][S::FD];
 };
 
-template <int LA, int LB, int LC, int LD, int GA, int GB, int GC, int GD>
-__device__ __forceinline__ void jk_make_offsets(int ga, int gb, int gc, int gd,
-                                                JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD>> &o)
+template <int LA, int LB, int LC, int LD, int GA, int GB, int GC, int GD, class S>
+__device__ __forceinline__ void jk_make_offsets(int ga, int gb, int gc, int gd, JkOffsets<S> &o)
 {
-    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
 #pragma unroll
@@ -246,17 +248,40 @@ __device__ __forceinline__ void jk_group_sync(unsigned gmask)
 // Accumulates the thread's fragment T[EPT] of the contracted block (ab|cd)
 // over every primitive quartet (eq:rys0). `grp` is the group's shared
 // memory (G > 1), gmask the group's lane mask.
+// Root r (< NRE) of the operator: set 0 at T (1/r) or at theta T (erf);
+// for OP 2 set 1 is the erf part with negated weight. Returns u and w * pref.
+template <int NR, int OP, typename R>
+__device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, int r, const R *__restrict__ rys,
+                                           R &u, R &wp)
+{
+    R uu, ww;
+    if (OP == 0 || (OP == 2 && r < NR)) {
+        jk_rys_one<NR>(Tt, r, rys, uu, ww);
+        u = uu;
+        wp = ww * pref;
+    } else {
+        // theta = w^2 / (w^2 + rho), sqrt(theta) = w / sqrt(w^2 + rho)
+        const R om = (R)omega;
+        const R rd = jk_rsqrt(om * om + rho);
+        const R st = om * rd, th = st * st;
+        jk_rys_one<NR>(th * Tt, OP == 2 ? r - NR : r, rys, uu, ww);
+        u = th * uu;
+        wp = (OP == 2 ? -st : st) * ww * pref;
+    }
+}
+
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
-          int GA, int GB, int GC, int GD, typename R>
-__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, double qthr,
+          int GA, int GB, int GC, int GD, typename R, int OP = 0>
+__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, double qthr, double omega,
                                            const typename JkPP<R>::T *__restrict__ pp,
                                            const R *__restrict__ rys, R *grp, unsigned gmask, int tg, bool act,
-                                           const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD>> &off,
-                                           R (&T)[JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::EPT])
+                                           const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>> &off,
+                                           R (&T)[JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>::EPT])
 {
-    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
+    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP> S;
     typedef typename JkPP<R>::T PPT;
     constexpr int NR = S::NR;
+    constexpr int NRE = S::NRE;
     const R ABx = (R)bra.ABx, ABy = (R)bra.ABy, ABz = (R)bra.ABz;
     const R CDx = (R)ket.ABx, CDy = (R)ket.ABy, CDz = (R)ket.ABz;
     const PPT *bpp = pp + bra.pp_off;
@@ -283,9 +308,9 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
             const R qf = q * inv_pq, pf = p * inv_pq;
             if (S::G == 1) {
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    R u, w;
-                    jk_rys_one<NR>(Tt, r, rys, u, w);
+                for (int r = 0; r < NRE; ++r) {
+                    R u, wp;
+                    jk_op_root<NR, OP, R>(Tt, rho, pref, omega, r, rys, u, wp);
                     const R b00 = (R)0.5 * u * inv_pq;
                     const R b10 = bp.inv2p * ((R)1 - u * qf);
                     const R b01 = kp.inv2p * ((R)1 - u * pf);
@@ -293,7 +318,7 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
                     R tx[S::NI], ty[S::NI], tz[S::NI];
                     jk_build_2d<LA, LB, LC, LD, R>(bp.PAx - uq * PQx, kp.PAx + up * PQx, b10, b01, b00, (R)1, ABx, CDx, tx);
                     jk_build_2d<LA, LB, LC, LD, R>(bp.PAy - uq * PQy, kp.PAy + up * PQy, b10, b01, b00, (R)1, ABy, CDy, ty);
-                    jk_build_2d<LA, LB, LC, LD, R>(bp.PAz - uq * PQz, kp.PAz + up * PQz, b10, b01, b00, w * pref, ABz, CDz, tz);
+                    jk_build_2d<LA, LB, LC, LD, R>(bp.PAz - uq * PQz, kp.PAz + up * PQz, b10, b01, b00, wp, ABz, CDz, tz);
 #pragma unroll
                     for (int ia = 0; ia < S::FA; ++ia)
 #pragma unroll
@@ -313,15 +338,15 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
                                 }
                 }
             } else {
-                R *roots = grp + NR * 3 * S::NI;   // [0, NR): u ; [NR, 2NR): w * pref
-                for (int r = tg; r < NR; r += S::G) {
-                    R u, w;
-                    jk_rys_one<NR>(Tt, r, rys, u, w);
+                R *roots = grp + NRE * 3 * S::NI;   // [0, NRE): u ; [NRE, 2 NRE): w * pref
+                for (int r = tg; r < NRE; r += S::G) {
+                    R u, wp;
+                    jk_op_root<NR, OP, R>(Tt, rho, pref, omega, r, rys, u, wp);
                     roots[r] = u;
-                    roots[NR + r] = w * pref;
+                    roots[NRE + r] = wp;
                 }
                 jk_group_sync<S::G>(gmask);
-                for (int task = tg; task < 3 * NR; task += S::G) {
+                for (int task = tg; task < 3 * NRE; task += S::G) {
                     const int r = task / 3, dir = task - 3 * r;
                     const R u = roots[r];
                     const R b00 = (R)0.5 * u * inv_pq;
@@ -331,7 +356,7 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
                     R pa, qc, pqd, abd, cdd, i00 = (R)1;
                     if (dir == 0) { pa = bp.PAx; qc = kp.PAx; pqd = PQx; abd = ABx; cdd = CDx; }
                     else if (dir == 1) { pa = bp.PAy; qc = kp.PAy; pqd = PQy; abd = ABy; cdd = CDy; }
-                    else { pa = bp.PAz; qc = kp.PAz; pqd = PQz; abd = ABz; cdd = CDz; i00 = roots[NR + r]; }
+                    else { pa = bp.PAz; qc = kp.PAz; pqd = PQz; abd = ABz; cdd = CDz; i00 = roots[NRE + r]; }
                     jk_build_2d<LA, LB, LC, LD, R>(pa - uq * pqd, qc + up * pqd, b10, b01, b00, i00, abd, cdd,
                                                    grp + (r * 3 + dir) * S::NI);
                 }
@@ -351,7 +376,7 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
                                 const int k = ((ia * S::FB + ib) * S::FC + ic) * S::FD + id;
                                 R acc = (R)0;
 #pragma unroll
-                                for (int r = 0; r < NR; ++r)
+                                for (int r = 0; r < NRE; ++r)
                                     acc += grp[(r * 3 + 0) * S::NI + ox] * grp[(r * 3 + 1) * S::NI + oy] *
                                            grp[(r * 3 + 2) * S::NI + oz];
                                 T[k] += acc;
@@ -585,12 +610,12 @@ __device__ __forceinline__ int jk_item_bra(const JkClassArgs &args, long long t)
 // Persistent: warps (or, for groups of more than 32 threads, whole CTAs)
 // take bra pairs from a global counter until none are left.
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
-          int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R, int MODE>
+          int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R, int MODE, int OP>
 __global__ void __launch_bounds__(JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G <= 32 ? 128
                                   : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G + 31) / 32) * 32)
 jk_class_kernel(const JkClassArgs args)
 {
-    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD> S;
+    typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP> S;
     constexpr int G = S::G;
     constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
     extern __shared__ double jk_smem_raw[];
@@ -607,7 +632,7 @@ jk_class_kernel(const JkClassArgs args)
         R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
-        jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
         for (;;) {
             long long t = 0;
             if (lane == 0) t = args.item_lo + (long long)atomicAdd(args.work, 1ull);
@@ -657,8 +682,8 @@ jk_class_kernel(const JkClassArgs args)
                         R T[S::EPT];
 #pragma unroll
                         for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
-                        const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(
-                            bra, ket, args.prim_eps / dmk, pp, rys, grp, gmask, tg, true, off, T);
+                        const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP>(
+                            bra, ket, args.prim_eps / dmk, args.omega, pp, rys, grp, gmask, tg, true, off, T);
                         if (tg == 0) nprim += np;
                         R f = (R)1;
                         if (bra.a == bra.b) f *= (R)0.5;
@@ -700,7 +725,7 @@ jk_class_kernel(const JkClassArgs args)
         const int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
         R *grp = reinterpret_cast<R *>(jk_smem_raw);
         JkOffsets<S> off;
-        jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
         for (;;) {
             if (threadIdx.x == 0) s_item = args.item_lo + (long long)atomicAdd(args.work, 1ull);
             __syncthreads();
@@ -752,8 +777,8 @@ jk_class_kernel(const JkClassArgs args)
                     R T[S::EPT];
 #pragma unroll
                     for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
-                    const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R>(
-                        bra, ket, args.prim_eps / s_dm[myket - base], pp, rys, grp, 0u, tg, act, off, T);
+                    const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP>(
+                        bra, ket, args.prim_eps / s_dm[myket - base], args.omega, pp, rys, grp, 0u, tg, act, off, T);
                     nprim += np;
                     if (act) {
                         R f = (R)1;
@@ -820,7 +845,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
         double *grp = jk_smem_raw + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
-        jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
         const int warps_total = (gridDim.x * blockDim.x) >> 5;
         const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         for (int base = gwarp * NGW; base < args.npair; base += warps_total * NGW) {
@@ -832,7 +857,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
                 double T[S::EPT];
 #pragma unroll
                 for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
+                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, 0.0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
                 if (ga == gc && gb == gd) {
 #pragma unroll
                     for (int ia = 0; ia < FA; ++ia)
@@ -854,13 +879,13 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
         const int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
         double *grp = jk_smem_raw;
         JkOffsets<S> off;
-        jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD>(ga, gb, gc, gd, off);
+        jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
         for (int pi = blockIdx.x; pi < args.npair; pi += gridDim.x) {
             const JkPair pr = args.pairs[pi];
             double T[S::EPT];
 #pragma unroll
             for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
+            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, 0.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
             double mx = 0.0;
             if (act && ga == gc && gb == gd) {
 #pragma unroll

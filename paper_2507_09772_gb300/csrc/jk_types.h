@@ -70,6 +70,7 @@ struct JkClassArgs {
     long long item_lo, item_hi;  // this build's share of the items [lo, hi) (partitioned builds)
     int chunk;                   // kets per work item (the last item of a bra runs to ket_end)
     double prim_eps;             // skip primitive quartets with q_ij q_kl Dmax <= prim_eps
+    double omega;                // |w| of the range-separated operator (OP 1, 2)
     unsigned long long *stats;   // [0] quartets, [1] primitive quartets, [2] routed band quartets
     int *err;                    // device error word
     double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi

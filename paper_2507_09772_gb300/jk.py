@@ -119,7 +119,7 @@ def load_library() -> ctypes.CDLL:
     lib.jk_info.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.jk_schwarz.argtypes = [vp, dp]
     lib.jk_destroy.argtypes = [vp]
-    lib.jk_compile_class.argtypes = [i32] * 13 + [P(i32), dp]
+    lib.jk_compile_class.argtypes = [i32] * 14 + [P(i32), dp]
     lib.jk_profile.argtypes = [vp, P(JkLaunchProf), i32, P(i32)]
     lib.jk_router_collect.argtypes = [vp, P(vp), i32, ctypes.c_double, P(vp), P(vp), vp, vp, ctypes.c_int64,
                                       P(ctypes.c_int64), vp]
@@ -312,10 +312,10 @@ def jk_measure_peak(which: str = "fp64", ms: float = 200.0) -> float:
     return v.value
 
 
-def jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm=1, with_j=1, with_k=1, fp32=0, mode=0):
+def jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm=1, with_j=1, with_k=1, fp32=0, mode=0, op=0):
     g = ctypes.c_int32()
     ms = ctypes.c_double()
-    _check(load_library().jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm, with_j, with_k, fp32, mode,
+    _check(load_library().jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm, with_j, with_k, fp32, mode, op,
                                            ctypes.byref(g), ctypes.byref(ms)))
     return g.value, ms.value
 

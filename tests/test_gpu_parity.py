@@ -307,8 +307,8 @@ def test_primitive_screening_changes_nothing_beyond_its_threshold():
     mol = synth.batched_molecule(9, natm=14)
     eng = jk.JK(mol)
     D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
-    J1, K1, s1 = eng.build(D, stats=True)                 # default: prim_eps = 1e-3 * cutoff
-    eng.set_option("prim_eps_rel", 0.0)
+    J1, K1, s1 = eng.build(D, stats=True)                 # default: prim_eps = 1e-16
+    eng.set_option("prim_eps", 0.0)
     J0, K0, s0 = eng.build(D, stats=True)                 # every primitive quartet
     torch.cuda.synchronize()
     eng.close()
@@ -316,3 +316,50 @@ def test_primitive_screening_changes_nothing_beyond_its_threshold():
     assert s1["prim_quartets"] < s0["prim_quartets"]
     assert float((J1 - J0).abs().max()) <= 1e-12
     assert float((K1 - K0).abs().max()) <= 1e-12
+
+
+@pytest.mark.parametrize("omega", [0.3, -0.3, 2.0])
+def test_range_separated_operators_match_oracle(omega):
+    mol = synth.random_small_molecule(51, natm=2, lmax=2, max_nprim=2)
+    J, K, _ = gpu_jk(mol, cutoff=1e-13, options={"omega": omega})
+    with oracle.omega_operator(omega):
+        Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    check(mol, J, Jr, TOL64, "J")
+    check(mol, K, Kr, TOL64, "K")
+
+
+def test_long_plus_short_range_is_coulomb():
+    mol = synth.tiny_631gs()
+    Jf, Kf, _ = gpu_jk(mol, cutoff=1e-13)
+    Jl, Kl, _ = gpu_jk(mol, cutoff=1e-13, options={"omega": 0.4})
+    Js, Ks, _ = gpu_jk(mol, cutoff=1e-13, options={"omega": -0.4})
+    assert np.abs(Jl + Js - Jf).max() <= 1e-11
+    assert np.abs(Kl + Ks - Kf).max() <= 1e-11
+
+
+def test_incremental_density_build_screens_on_the_change():
+    """Direct-SCF incremental build (Sec. 2, density screening with Delta D):
+    J(D2) = J(D1) + J(D2 - D1), the increment screened by |D2 - D1|."""
+    mol = synth.batched_molecule(10, natm=12)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((mol.nao, mol.nao)) * 1e-4
+    D1 = mol.D
+    D2 = D1 + (X + X.T)[None]
+    J1, K1, s1 = gpu_jk(mol, D=D1, cutoff=1e-13)
+    Jd, Kd, sd = gpu_jk(mol, D=D2 - D1, cutoff=1e-13)
+    J2, K2, s2 = gpu_jk(mol, D=D2, cutoff=1e-13)
+    assert np.abs(J1 + Jd - J2).max() <= 1e-10
+    assert np.abs(K1 + Kd - K2).max() <= 1e-10
+    assert sd["quartets_fp64"] < 0.8 * s2["quartets_fp64"]
+
+
+def test_separate_j_and_k_builds_screen_on_their_own_blocks():
+    mol = synth.batched_molecule(11, natm=16)
+    _, _, sjk = gpu_jk(mol, cutoff=1e-13)
+    J, _, sj = gpu_jk(mol, cutoff=1e-13, with_k=False)
+    _, K, sk = gpu_jk(mol, cutoff=1e-13, with_j=False)
+    assert sj["quartets_fp64"] <= sjk["quartets_fp64"] and sk["quartets_fp64"] <= sjk["quartets_fp64"]
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13, with_k=False)
+    assert np.abs(J - Jr).max() <= TOL64
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13, with_j=False)
+    assert np.abs(K - Kr).max() <= TOL64

@@ -27,8 +27,12 @@ MUTATIONS = {
                           "term *= 2.0 * T / (2 * mmax + 2 * k - 1);"),
     "boys_upward_sign": ("F[m + 1] = ((2 * m + 1) * F[m] - e) / (2.0 * T);",
                          "F[m + 1] = ((2 * m + 1) * F[m] + e) / (2.0 * T);"),
-    "prefactor": ("double pref = scale * 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));",
-                  "double pref = scale * 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p * q));"),
+    "prefactor": ("double pref = scale * sqrt(theta) * 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q));",
+                  "double pref = scale * sqrt(theta) * 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p * q));"),
+    "range_separation_theta": ("double theta = omega > 0.0 ? omega * omega / (omega * omega + rho) : 1.0;",
+                               "double theta = omega > 0.0 ? omega * omega / (omega * omega + p) : 1.0;"),
+    "range_separation_prefactor": ("double pref = scale * sqrt(theta) * 2.0",
+                                   "double pref = scale * theta * 2.0"),
     "degeneracy_factor_dropped": ("if (p1 == p2) f *= 0.5;", ""),
     "K_update_wrong_density": ("Yk[I * nao + L] += v * Dk[Jx * nao + Kx];",
                                "Yk[I * nao + L] += v * Dk[Jx * nao + L];"),

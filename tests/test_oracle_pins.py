@@ -185,7 +185,10 @@ def _pair_1d_tables(u, la, lb, lc, ld, a, b, c, d, A, B, C, D):
     return out
 
 
-def quadrature_eri(ls, al, R):
+def quadrature_eri(ls, al, R, u_lo=0.0, u_hi=None):
+    """Gaussian-transform quadrature of (ab|cd) for the operator
+    (2/sqrt(pi)) int_{u_lo}^{u_hi} exp(-u^2 r^2) du: 1/r for [0, inf),
+    erf(w r)/r for [0, w], erfc(w r)/r for [w, inf)."""
     la, lb, lc, ld = ls
     ca, cb, cc, cd = (oracle.cart_components(l) for l in ls)
 
@@ -203,12 +206,14 @@ def quadrature_eri(ls, al, R):
                         blk[i, j, k, l] = v
         return blk.ravel()
 
-    # 1/r12 = (2/sqrt(pi)) int_0^inf exp(-u^2 r12^2) du; map u = s/(1-s)
-    def mapped(s):
-        u = s / (1.0 - s)
-        return integrand(u) / (1.0 - s) ** 2
-
-    val, err = integrate.quad_vec(mapped, 0.0, 1.0, epsabs=1e-14, epsrel=1e-11, limit=400)
+    # 1/r12 = (2/sqrt(pi)) int_0^inf exp(-u^2 r12^2) du; map u = u_lo + s/(1-s)
+    if u_hi is None:
+        def mapped(s):
+            u = u_lo + s / (1.0 - s)
+            return integrand(u) / (1.0 - s) ** 2
+        val, err = integrate.quad_vec(mapped, 0.0, 1.0, epsabs=1e-14, epsrel=1e-11, limit=400)
+    else:
+        val, err = integrate.quad_vec(integrand, u_lo, u_hi, epsabs=1e-14, epsrel=1e-11, limit=400)
     return 2.0 / math.sqrt(math.pi) * val.reshape(len(ca), len(cb), len(cc), len(cd))
 
 
@@ -421,3 +426,64 @@ def test_spherical_trace_identity():
                                                                   rel=1e-12)
     assert np.einsum("ij,ij->", mol.D[0], K[0]) == pytest.approx(np.einsum("ij,ij->", Dc, Kc[0]),
                                                                   rel=1e-12)
+
+
+# ------------------------------------------------- range-separated Coulomb
+@pytest.mark.parametrize("omega", [0.2, 0.7, 3.0])
+def test_long_range_ssss_closed_form(omega):
+    rng = np.random.default_rng(int(omega * 10))
+    for _ in range(10):
+        al = np.exp(rng.uniform(np.log(0.05), np.log(50.0), size=4))
+        R = _rng_centers(rng)
+        a, b, c, d = al
+        p, q = a + b, c + d
+        P = (a * R[0] + b * R[1]) / p
+        Q = (c * R[2] + d * R[3]) / q
+        Kab = math.exp(-a * b / p * np.sum((R[0] - R[1]) ** 2))
+        Kcd = math.exp(-c * d / q * np.sum((R[2] - R[3]) ** 2))
+        rho = p * q / (p + q)
+        theta = omega ** 2 / (omega ** 2 + rho)
+        T = theta * rho * np.sum((P - Q) ** 2)
+        F0 = 1.0 if T == 0 else 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+        ref = 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * Kab * Kcd * math.sqrt(theta) * F0
+        with oracle.omega_operator(omega):
+            val = oracle.eri_prim((0, 0, 0, 0), al, R)[0, 0, 0, 0]
+        assert val == pytest.approx(ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("ls", [(1, 0, 0, 0), (1, 1, 1, 0), (2, 1, 0, 1), (2, 2, 1, 1)])
+@pytest.mark.parametrize("omega", [0.4, -0.4, 1.5, -1.5])
+def test_range_separated_against_quadrature(ls, omega):
+    rng = np.random.default_rng(sum(ls) + int(abs(omega) * 10))
+    al = np.exp(rng.uniform(np.log(0.2), np.log(3.0), size=4))
+    R = _rng_centers(rng, 1.0)
+    w = abs(omega)
+    ref = quadrature_eri(ls, al, R, 0.0, w) if omega > 0 else quadrature_eri(ls, al, R, w, None)
+    with oracle.omega_operator(omega):
+        got = oracle.eri_prim(ls, al, R)
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_long_range_tends_to_full_coulomb():
+    rng = np.random.default_rng(3)
+    al = np.exp(rng.uniform(np.log(0.2), np.log(3.0), size=4))
+    R = _rng_centers(rng, 1.0)
+    full = oracle.eri_prim((2, 1, 1, 0), al, R)
+    with oracle.omega_operator(1e6):
+        lr = oracle.eri_prim((2, 1, 1, 0), al, R)
+    assert np.abs(lr - full).max() < 1e-9 * np.abs(full).max()
+
+
+def test_range_separated_jk_is_symmetric_and_ordered():
+    mol = synth.tiny_631gs()
+    Jf, Kf, _ = oracle.jk(mol, cutoff=0.0)
+    with oracle.omega_operator(0.3):
+        Jl, Kl, _ = oracle.jk(mol, cutoff=0.0)
+    with oracle.omega_operator(-0.3):
+        Js, Ks, _ = oracle.jk(mol, cutoff=0.0)
+    assert np.abs(Jl + Js - Jf).max() < 1e-12
+    assert np.abs(Kl + Ks - Kf).max() < 1e-12
+    D = mol.D[0]
+    # both attenuated operators are positive definite
+    for J in (Jl, Js):
+        assert np.einsum("ij,ij->", D, J[0]) > 0
