@@ -261,6 +261,14 @@ int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na,
                      int32_t nd, int32_t n_dm, int32_t with_j, int32_t with_k, int32_t fp32, int32_t mode,
                      int32_t op, int32_t *threads_per_quartet, double *compile_ms);
 
+/* Ahead-of-time compilation (no GPU needed) of every kernel a basis with
+ * these shell types needs: the Schwarz kernels (contracted and primitive)
+ * and the class kernels for n_dm, the flags, fp32 and mode (as in
+ * jk_compile_class, operator 1/r), in parallel, into the disk cache.
+ * *nkernels receives the number of kernels considered. */
+int jk_compile_basis(const jk_shell *shells, int32_t nshell, int32_t n_dm, int32_t with_j, int32_t with_k,
+                     int32_t fp32, int32_t mode, double *compile_ms, int32_t *nkernels);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *jk_last_error(void);
 

@@ -1867,6 +1867,57 @@ int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na,
     }
 }
 
+int jk_compile_basis(const jk_shell *shells, int32_t nshell, int32_t n_dm, int32_t with_j, int32_t with_k,
+                     int32_t fp32, int32_t mode, double *compile_ms, int32_t *nkernels)
+{
+    if (!shells || nshell < 1) return fail(JK_ERR_ARG, "no shells");
+    if (n_dm < 1 || n_dm > JK_NDM_MAX || (!with_j && !with_k)) return fail(JK_ERR_ARG, "bad n_dm or flags");
+    if (mode < 0 || mode > 2 || (mode == 2 && fp32)) return fail(JK_ERR_ARG, "bad mode");
+    // shell types (l, nprim) -> pair classes (larger type first) -> class pairs
+    std::vector<std::pair<int, int>> types;
+    for (int i = 0; i < nshell; ++i) {
+        if (shells[i].l < 0 || shells[i].l > JK_LMAX || shells[i].nprim < 1 || shells[i].nprim > JK_NPRIM_MAX)
+            return fail(JK_ERR_UNSUPPORTED, "shell %d out of range", i);
+        types.push_back({shells[i].l, shells[i].nprim});
+    }
+    std::sort(types.begin(), types.end());
+    types.erase(std::unique(types.begin(), types.end()), types.end());
+    std::reverse(types.begin(), types.end());
+    std::vector<std::pair<int, int>> pcs;   // indices into types, a <= b (a is the larger type)
+    for (size_t a = 0; a < types.size(); ++a)
+        for (size_t b = a; b < types.size(); ++b) pcs.push_back({(int)a, (int)b});
+    std::vector<KSpec> specs;
+    for (auto &pc : pcs) {
+        KSpec s;
+        s.kind = 1;
+        s.la = s.lc = types[pc.first].first; s.lb = s.ld = types[pc.second].first;
+        s.na = s.nc = types[pc.first].second; s.nb = s.nd = types[pc.second].second;
+        choose_fragments(s, true);
+        specs.push_back(s);
+        s.na = s.nb = s.nc = s.nd = 1;
+        choose_fragments(s, true);
+        specs.push_back(s);
+    }
+    for (size_t i = 0; i < pcs.size(); ++i)
+        for (size_t j = i; j < pcs.size(); ++j) {
+            KSpec s;
+            s.kind = 0;
+            s.la = types[pcs[i].first].first; s.lb = types[pcs[i].second].first;
+            s.lc = types[pcs[j].first].first; s.ld = types[pcs[j].second].first;
+            s.na = types[pcs[i].first].second; s.nb = types[pcs[i].second].second;
+            s.nc = types[pcs[j].first].second; s.nd = types[pcs[j].second].second;
+            s.ndm = n_dm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0; s.fp32 = fp32 ? 1 : 0; s.mode = mode;
+            choose_fragments(s, false);
+            specs.push_back(s);
+        }
+    if (nkernels) *nkernels = (int32_t)specs.size();
+    try {
+        return compile_to_disk(specs, compile_ms);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_COMPILE, "host exception: %s", e.what());
+    }
+}
+
 const char *jk_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

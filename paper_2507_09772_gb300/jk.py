@@ -27,7 +27,7 @@ EXPORTED = ["jk_init", "jk_init_batch", "jk_build", "jk_build_batch", "jk_set_op
             "jk_get_option", "jk_info", "jk_schwarz", "jk_destroy", "jk_router_collect", "jk_router_train",
             "jk_router_forward", "jk_router_gradient", "jk_router_gradient_noalloc", "jk_router_load",
             "jk_profile", "jk_measure_peak",
-            "jk_compile_class", "jk_last_error"]
+            "jk_compile_class", "jk_compile_basis", "jk_last_error"]
 
 ROUTER_NIN = 12
 ROUTER_NPARAM = 5313
@@ -121,6 +121,7 @@ def load_library() -> ctypes.CDLL:
     lib.jk_destroy.argtypes = [vp]
     lib.jk_compile_class.argtypes = [i32] * 14 + [P(i32), dp]
     lib.jk_profile.argtypes = [vp, P(JkLaunchProf), i32, P(i32)]
+    lib.jk_compile_basis.argtypes = [P(JkShell), i32, i32, i32, i32, i32, i32, dp, P(i32)]
     lib.jk_router_collect.argtypes = [vp, P(vp), i32, ctypes.c_double, P(vp), P(vp), vp, vp, ctypes.c_int64,
                                       P(ctypes.c_int64), vp]
     lib.jk_router_train.argtypes = [vp, vp, ctypes.c_int64, P(JkTrainOpts), P(JkRouterBlob), P(JkTrainStats)]
@@ -312,6 +313,16 @@ def jk_measure_peak(which: str = "fp64", ms: float = 200.0) -> float:
     return v.value
 
 
+def jk_compile_basis(shells, n_dm=1, with_j=1, with_k=1, fp32=0, mode=0):
+    """Compile every kernel a basis of these shell types needs (no GPU needed)."""
+    sh = _shell_array(shells)
+    ms = ctypes.c_double()
+    nk = ctypes.c_int32()
+    _check(load_library().jk_compile_basis(sh, len(sh), n_dm, with_j, with_k, fp32, mode, ctypes.byref(ms),
+                                           ctypes.byref(nk)))
+    return nk.value, ms.value
+
+
 def jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm=1, with_j=1, with_k=1, fp32=0, mode=0, op=0):
     g = ctypes.c_int32()
     ms = ctypes.c_double()
@@ -368,10 +379,7 @@ class JK:
         Returns (J, K, stats-or-None); J/K allocated with torch if not given."""
         import torch
         mode = PRECISION[precision] if isinstance(precision, str) else int(precision)
-        if self.nmol == 1:
-            Dl = [D]
-        else:
-            Dl = list(D)
+        Dl = list(D) if isinstance(D, (list, tuple)) else [D]
         Dl = [d if d.dim() == 3 else d.unsqueeze(0) for d in Dl]
         ndm = Dl[0].shape[0]
         if J is None and with_j:
@@ -379,10 +387,13 @@ class JK:
         if K is None and with_k:
             K = [torch.empty_like(d) for d in Dl]
         if self.nmol == 1:
+            listed = isinstance(D, (list, tuple))
             Jl = J if isinstance(J, list) else [J]
             Kl = K if isinstance(K, list) else [K]
             st = jk_build(self.h, Dl[0], ndm, with_j, with_k, cutoff, mode,
                           Jl[0] if with_j else None, Kl[0] if with_k else None, stream, stats)
+            if listed:
+                return (Jl if with_j else None), (Kl if with_k else None), st
             return (Jl[0] if with_j else None), (Kl[0] if with_k else None), st
         st = jk_build_batch(self.h, Dl, ndm, with_j, with_k, cutoff, mode,
                             J if with_j else None, K if with_k else None, stream, stats)

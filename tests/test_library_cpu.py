@@ -81,3 +81,12 @@ def test_compile_rejects_out_of_range(lib):
     with pytest.raises(jk.JKError) as e:
         jk.jk_compile_class(5, 0, 0, 0, 1, 1, 1, 1)
     assert e.value.code == jk.JK_ERR_UNSUPPORTED
+
+
+def test_compile_basis_builds_every_kernel_of_a_basis(lib, tmp_path, monkeypatch):
+    monkeypatch.setenv("JK_KERNEL_CACHE", str(tmp_path))
+    shells = np.array([[0, 1, 2, 0, 0, 0], [0, 0, 3, 2, 3, 0]], dtype=np.int32)   # p2, s3
+    nk, ms = jk.jk_compile_basis(shells)
+    # 3 pair classes: 2 Schwarz kernels each (contracted, primitive) + 6 class pairs
+    assert nk == 3 * 2 + 6
+    assert len(list(tmp_path.iterdir())) == nk
