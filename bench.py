@@ -60,9 +60,11 @@ def parse():
     ap.add_argument("--no-probe", action="store_true", help="skip the FMA peak probes (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
     ap.add_argument("--form-steps", type=int, default=2)
-    ap.add_argument("--tau32", type=float, default=1e-7)
+    ap.add_argument("--tau32", type=float, default=1e-4)
     ap.add_argument("--graph", type=int, default=1, help="replay each build as one CUDA graph")
     ap.add_argument("--branches", type=int, default=4, help="class kernels forked over this many graph branches")
+    ap.add_argument("--tune", type=int, default=1, help="autotune the fragment shapes before the warm-up (untimed)")
+    ap.add_argument("--prof-steps", type=int, default=1, help="serialised, per-kernel-timed steps after the timed region")
     return ap.parse_args()
 
 
@@ -231,7 +233,9 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets
                 "fp32_fraction": st["quartets_fp32"] / max(1, q), "quartets_routed": st["quartets_routed"],
                 "same_quartets_as_fp64": bool(q == fp64_quartets)}
 
+    tune = eng.autotune(Ds, cutoff=args.cutoff, precision="mixed") if args.tune else None
     out["mixed"] = timed("mixed")
+    out["mixed"]["autotune"] = tune
     # router: labels from FP64 logging builds of held-out molecules shaped
     # like the batched and cluster workloads (not the ones timed here),
     # trained on the GPU, then routed builds of the workload
@@ -300,6 +304,10 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tune = None
+    if args.tune:
+        tune = eng.autotune(Ds, cutoff=args.cutoff, precision=args.precision)
+
     def step(stats=True):
         flush.fill_(1)
         _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=args.precision, J=Js, K=Ks, stats=stats)
@@ -310,7 +318,6 @@ def run_ours(args):
     first_s = time.perf_counter() - t0
     for _ in range(max(0, args.warmup - 1)):
         step()
-    eng.set_option("profile", 1)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -320,10 +327,24 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     stats = []
-    prof = {}
     for _ in range(args.steps):
-        st = step()
-        stats.append(st)
+        stats.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+
+    # Per-kernel launch durations: CUDA events around every class kernel, on
+    # the stream it runs on, in steps replayed with the kernels serialised
+    # (one graph branch) so that no two class kernels share the GPU.
+    eng.set_option("profile", 1)
+    eng.set_option("branches", 1)
+    prof = {}
+    e0.record(stream)
+    for _ in range(args.prof_steps):
+        step()
         for p in jk.jk_profile(eng.h):
             key = (p["la"], p["lb"], p["lc"], p["ld"], p["na"], p["nb"], p["nc"], p["nd"], p["tier"])
             agg = prof.setdefault(key, dict(p, ms=0.0, flops_model=0.0, quartets=0, launches=0))
@@ -333,11 +354,9 @@ def run_ours(args):
             agg["launches"] += 1
     e1.record(stream)
     torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    clocks = sampler.stop()
-    ms_total = e0.elapsed_time(e1)
+    ms_serial = e0.elapsed_time(e1)
     eng.set_option("profile", 0)
+    eng.set_option("branches", args.branches)
     quartets = sum(s["quartets_fp64"] + s["quartets_fp32"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
     if pg:
@@ -360,7 +379,9 @@ def run_ours(args):
         "kernel": "jk_class_kernel<(%d%d|%d%d) prims %d%d%d%d, %s>" % (
             dom["la"], dom["lb"], dom["lc"], dom["ld"], dom["na"], dom["nb"], dom["nc"], dom["nd"],
             "fp64" if dom["tier"] == 0 else "fp32"),
-        "kernel_share": dom["ms"] / ms_total,
+        "kernel_share": dom["ms"] / ms_serial,
+        "launch_ms": dom_ms, "launches": dom["launches"],
+        "timing": "CUDA events around each launch, serialised replay after the timed region",
         "peak_source": "nominal FP64 FMA rate: 152 SMs x 4 FLOP/clk x 2.07 GHz" if dom["tier"] == 0
         else "nominal FP32 FMA rate: 152 SMs x 256 FLOP/clk x 2.07 GHz",
         "peak_probe_tflops": probe / 1e12, "frac_of_probe": dom_flops / (dom_ms * 1e-3) / probe,
@@ -435,6 +456,8 @@ def run_ours(args):
             "prim_quartets_per_step": sum(s["prim_quartets"] for s in stats) / args.steps,
             "model_flops_per_step": sum(s["flops_model"] for s in stats) / args.steps,
             "path_fp64_roofline": path_fp64,
+            "autotune": tune,
+            "serial_ms_per_step": ms_serial / args.prof_steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "forms": forms,
@@ -448,8 +471,8 @@ def run_ours(args):
             "peak_probe_fp32_tflops": None if args.no_probe else jk.jk_measure_peak("fp32", 100.0) / 1e12,
             "top_kernels": sorted(
                 [{"class": "(%d%d|%d%d)/%d%d%d%d" % (v["la"], v["lb"], v["lc"], v["ld"], v["na"], v["nb"], v["nc"], v["nd"]),
-                  "tier": v["tier"], "ms_per_step": v["ms"] / args.steps, "share": v["ms"] / ms_total,
-                  "quartets_per_step": v["quartets"] / args.steps,
+                  "tier": v["tier"], "ms_per_step": v["ms"] / args.prof_steps, "share": v["ms"] / ms_serial,
+                  "quartets_per_step": v["quartets"] / args.prof_steps,
                   "tflops_model": v["flops_model"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0,
                   "G": v["threads_per_quartet"], "regs": v["regs"], "local_bytes": v["local_bytes"]}
                  for v in prof.values()], key=lambda x: -x["ms_per_step"])[:12],

@@ -161,7 +161,7 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
                    void *stream, jk_stats *stats);
 
 /* Options (double-valued): "tau32" (FP32 tier threshold on Q_ab Q_cd Dmax,
- * default 1e-7), "router_band" (K, default 100), "pair_cutoff" (shell pairs
+ * default 1e-4), "router_band" (K, default 100), "pair_cutoff" (shell pairs
  * with Q_ab at or below it are dropped at init, default 1e-18),
  * "use_graph" (0/1), "use_dmax" (0/1: 0 screens with Dmax := 1),
  * "profile" (0/1: CUDA events around every integral launch, see jk_profile;
@@ -268,6 +268,43 @@ int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na,
  * *nkernels receives the number of kernels considered. */
 int jk_compile_basis(const jk_shell *shells, int32_t nshell, int32_t n_dm, int32_t with_j, int32_t with_k,
                      int32_t fp32, int32_t mode, double *compile_ms, int32_t *nkernels);
+
+/* Result of jk_autotune. */
+typedef struct {
+    int32_t launches_tuned;    /* class-pair launches (per tier) that had more than one candidate */
+    int32_t candidates_timed;  /* candidate kernels timed in all */
+    int32_t changed;           /* launches whose fragment shape changed */
+    int32_t pad;
+    double ms_before;          /* summed launch times of those launches with their previous shapes */
+    double ms_after;           /* ... with the chosen shapes */
+    double tune_s;             /* wall time of the tuning, compilation included */
+} jk_tune_report;
+
+/* Autotuner: the per-device grid search over fragmentations (threads per
+ * quartet and how they split the four shells' Cartesian components) of
+ * Sec. 3.2 of arXiv 2507.09772, run on the caller's data. Every class-pair
+ * launch of the tiers `precision_mode` uses whose estimated share of the
+ * work is at least min_share gets up to max_candidates (1..16) shapes
+ * (jk_fragment_candidates); each is timed by CUDA events around its launch in
+ * two serialised builds of D (arguments as jk_build_batch: n_dm densities per
+ * molecule, J and K device buffers of the same shape, overwritten), and the
+ * fastest is kept. The choices stay in the handle (captured graphs are
+ * dropped) and are written to the tuning table (a text file named for the
+ * device model in $JK_TUNING_DIR, else in the kernel cache directory), which
+ * later jk_init calls on the same device model read. The
+ * call synchronises `stream`. report may be NULL. */
+int jk_autotune(jk_handle *h, const double *const *D, int32_t n_dm, int with_j, int with_k, double cutoff,
+                int precision_mode, double *const *J, double *const *K, void *stream, int32_t max_candidates,
+                double min_share, jk_tune_report *report);
+
+/* The autotuner's candidate shapes for class (la lb|lc ld) (fp32 = 1 for the
+ * FP32 tier): the built-in heuristic's shape first, then G = 1 where the class
+ * is small, then one shape per group size G = ga*gb*gc*gd (2..256, each g
+ * dividing its shell's Cartesian size, at most 64 elements per thread),
+ * nearest in log2 G first. frag: max_candidates x 4 (ga gb gc gd), host;
+ * *n receives the count. Needs no GPU. */
+int jk_fragment_candidates(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t fp32, int32_t max_candidates,
+                           int32_t *frag, int32_t *n);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *jk_last_error(void);

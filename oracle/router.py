@@ -4,7 +4,10 @@ TEST INFRASTRUCTURE (same rules as the rest of ``oracle/``).
 
 The router is a 12 -> 64 -> 64 -> 1 ReLU MLP whose weights are used in BF16
 (round to nearest even from the FP32 master copy) with the features
-normalised as (x - mu) * isd. It is trained with the pinball (quantile) loss
+normalised as (x - mu) * isd. The input of every layer (the normalised
+features, the two hidden activations) is rounded to BF16 as well, since the
+GPU evaluates the layers as BF16 tensor-core products; everything else is
+exact here (FP64). It is trained with the pinball (quantile) loss
 rho_q(u) = u (q - [u < 0]), u = y - prediction. This module evaluates the
 network and the loss gradient in FP64 from the same BF16-rounded weights, so
 that the GPU forward and backward kernels can be checked against it.
@@ -49,15 +52,22 @@ def unpack(theta: np.ndarray, round_weights: bool = True):
     return W1, b1, W2, b2, W3, b3
 
 
+def _layers(theta, mu, isd, X, round_weights):
+    """Forward pass; returns (xn, a1, h1, a2, h2, out, weights). With
+    round_weights the layer inputs xn, h1, h2 are BF16-rounded too."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta, round_weights)
+    ra = bf16_round if round_weights else (lambda x: x)
+    xn = ra((np.asarray(X, np.float64) - np.asarray(mu, np.float64)[:NIN]) * np.asarray(isd, np.float64)[:NIN])
+    a1 = xn @ W1 + b1
+    h1 = ra(np.maximum(a1, 0.0))
+    a2 = h1 @ W2 + b2
+    h2 = ra(np.maximum(a2, 0.0))
+    return xn, a1, h1, a2, h2, h2 @ W3 + b3, (W1, b1, W2, b2, W3, b3)
+
+
 def forward(theta, mu, isd, X, round_weights=True):
     """Prediction per row (without the routing margin), FP64."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta, round_weights)
-    xn = (np.asarray(X, np.float64) - np.asarray(mu, np.float64)[:NIN]) * np.asarray(isd, np.float64)[:NIN]
-    a1 = xn @ W1 + b1
-    h1 = np.maximum(a1, 0.0)
-    a2 = h1 @ W2 + b2
-    h2 = np.maximum(a2, 0.0)
-    return h2 @ W3 + b3
+    return _layers(theta, mu, isd, X, round_weights)[5]
 
 
 def pinball_loss(theta, mu, isd, X, y, q, round_weights=True):
@@ -70,16 +80,11 @@ def pinball_grad(theta, mu, isd, X, y, q, round_weights=True):
 
     The derivative is taken with respect to the weights as used (the BF16
     rounding is treated as the identity, a straight-through estimate), which
-    is what the GPU training kernels do."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta, round_weights)
+    is what the GPU training kernels do; the same holds for the rounding of
+    the layer inputs."""
     X = np.asarray(X, np.float64)
     n = X.shape[0]
-    xn = (X - np.asarray(mu, np.float64)[:NIN]) * np.asarray(isd, np.float64)[:NIN]
-    a1 = xn @ W1 + b1
-    h1 = np.maximum(a1, 0.0)
-    a2 = h1 @ W2 + b2
-    h2 = np.maximum(a2, 0.0)
-    out = h2 @ W3 + b3
+    xn, a1, h1, a2, h2, out, (W1, b1, W2, b2, W3, b3) = _layers(theta, mu, isd, X, round_weights)
     u = np.asarray(y, np.float64) - out
     loss = float(np.mean(np.where(u >= 0, q * u, (q - 1.0) * u)))
     g = ((u < 0).astype(np.float64) - q) / n           # d loss / d out, per row

@@ -22,17 +22,20 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cctype>
 #include <cstring>
 #include <fstream>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <sstream>
 #include <string>
 #include <thread>
@@ -104,6 +107,7 @@ struct KSpec {
     int kind = 0;  // 0 class kernel, 1 Schwarz kernel
     int la = 0, lb = 0, lc = 0, ld = 0, na = 1, nb = 1, nc = 1, nd = 1;
     int ga = 1, gb = 1, gc = 1, gd = 1;
+    int gx = 1;    // CTAs one group is split over (groups of more than 256 threads)
     int ndm = 1, doj = 1, dok = 1, fp32 = 0;
     int mode = 0;  // 0 plain, 1 routed (learned router in the band), 2 label logging
     int op = 0;    // 0 1/r, 1 erf(w r)/r, 2 erfc(w r)/r
@@ -112,18 +116,20 @@ struct KSpec {
     {
         char b[256];
         if (kind == 1)
-            snprintf(b, sizeof b, "jk_schwarz_kernel<%d,%d,%d,%d,%d,%d,%d,%d>", la, lb, na, nb, ga, gb, gc, gd);
+            snprintf(b, sizeof b, "jk_schwarz_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d>", la, lb, na, nb, ga, gb, gc, gd, gx);
         else
-            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s,%d,%d>", la, lb,
-                     lc, ld, na, nb, nc, nd, ga, gb, gc, gd, ndm, doj, dok, fp32 ? "float" : "double", mode, op);
+            snprintf(b, sizeof b, "jk_class_kernel<%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%s,%d,%d>", la,
+                     lb, lc, ld, na, nb, nc, nd, ga, gb, gc, gd, gx, ndm, doj, dok, fp32 ? "float" : "double", mode,
+                     op);
         return b;
     }
     int G() const { return ga * gb * gc * gd; }
     int nr() const { return ((la + lb + lc + ld) / 2 + 1) * (op == 2 ? 2 : 1); }
     int ni() const { return (la + 1) * (lb + 1) * (lc + 1) * (ld + 1); }
     int smem_group_reals() const { return G() == 1 ? 0 : nr() * 3 * ni() + 2 * nr(); }
-    // G <= 32: four warps, each holding 32/G groups; G > 32: one group per CTA
-    int block() const { return G() <= 32 ? 128 : ((G() + 31) / 32) * 32; }
+    // G <= 32: four warps, each holding 32/G groups; G > 32: one group (or
+    // one of its gx slabs) per CTA
+    int block() const { return G() <= 32 ? 128 : ((G() / gx + 31) / 32) * 32; }
     size_t smem_bytes() const
     {
         const size_t groups = G() <= 32 ? (size_t)4 * (32 / G()) : 1;
@@ -312,6 +318,12 @@ int ensure_kernels(const std::vector<KSpec> &specs, std::vector<KInfo> &out)
     CK(cudaGetDevice(&dev));
     KernelCache &kc = kcache();
     out.assign(specs.size(), KInfo());
+    // dynamic shared memory of a CTA: 227 KB on sm_103a, less a margin for
+    // the kernels' static shared variables
+    for (auto &sp : specs)
+        if (sp.smem_bytes() > 220 * 1024)
+            return fail(JK_ERR_UNSUPPORTED, "%s needs %zu bytes of shared memory per CTA (at most %d)",
+                        sp.name().c_str(), sp.smem_bytes(), 220 * 1024);
     std::vector<int> todo;
     std::vector<uint64_t> keys(specs.size());
     {
@@ -371,8 +383,14 @@ int ensure_kernels(const std::vector<KSpec> &specs, std::vector<KInfo> &out)
         r = d.moduleGetFunction(&ki.fn, mod, lowered[k].c_str());
         if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "cuModuleGetFunction(%s) failed: %d", s.name().c_str(), (int)r);
         ki.smem = s.smem_bytes();
-        if (ki.smem > 48 * 1024)
-            d.funcSetAttribute(ki.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)ki.smem);
+        // dynamic plus static shared memory above 48 KB needs the opt-in
+        // (the routed kernels add 1-4 KB of static router scratch)
+        if (ki.smem > 0) {
+            r = d.funcSetAttribute(ki.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)ki.smem);
+            if (r != CUDA_SUCCESS)
+                return fail(JK_ERR_UNSUPPORTED, "%s: %zu bytes of dynamic shared memory refused (%d)", s.name().c_str(),
+                            ki.smem, (int)r);
+        }
         d.funcGetAttribute(&ki.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ki.fn);
         d.funcGetAttribute(&ki.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, ki.fn);
         d.occupancy(&ki.blocks_per_sm, ki.fn, s.block(), ki.smem);
@@ -434,10 +452,20 @@ void choose_fragments(KSpec &s, bool symmetric)
     const int ne = nf[0] * nf[1] * nf[2] * nf[3];
     const int ni = s.ni();
     const int reg_cap = 48;                   // per-thread fragment budget (reals)
-    const int gmax = symmetric ? 1024 : 256;  // threads per quartet (one CTA at most)
+    const int gmax = symmetric ? 1024 : 256;  // threads per quartet in one CTA
+    const int gsplit = 256;                   // threads per CTA of a group split over CTAs
     const int g1_cap = s.fp32 ? 128 : 64;     // register-mode budget: fragment + 3 tables
+    s.gx = 1;
     if (ne + 3 * ni <= g1_cap) { s.ga = s.gb = s.gc = s.gd = 1; return; }
-    int best[4] = {1, 1, 1, 1};
+    // CTAs for a group of g threads: 1 if it fits one CTA, else the fewest
+    // x (<= 16) dividing g with g / x <= gsplit, 0 if there is none
+    auto split = [&](int g) {
+        if (g <= gmax) return 1;
+        for (int x = 2; x <= 16; ++x)
+            if (g % x == 0 && g / x <= gsplit) return x;
+        return 0;
+    };
+    int best[5] = {1, 1, 1, 1, 1};
     long best_score = -1;
     auto divisors = [](int n) { std::vector<int> v; for (int i = 1; i <= n; ++i) if (n % i == 0) v.push_back(i); return v; };
     for (int a : divisors(nf[0]))
@@ -445,16 +473,167 @@ void choose_fragments(KSpec &s, bool symmetric)
             for (int c : divisors(nf[2]))
                 for (int d : divisors(nf[3])) {
                     if (symmetric && (a != c || b != d)) continue;
-                    int g = a * b * c * d;
-                    if (g > gmax || g < 2) continue;
-                    int ept = ne / g;
-                    // prefer: fits the budget, then fewest threads, then fewest idle lanes
-                    long fits = ept <= reg_cap ? 1 : 0;
-                    long idle = g <= 32 ? 32 % g : (32 - g % 32) % 32;
-                    long score = fits * 100000000L + (fits ? (2000 - g) * 1000L : (1000000L - ept) * 10L) - idle;
-                    if (score > best_score) { best_score = score; best[0] = a; best[1] = b; best[2] = c; best[3] = d; }
+                    const int g = a * b * c * d;
+                    if (g < 2) continue;
+                    const int x = split(g);
+                    if (x == 0) continue;
+                    const int ept = ne / g;
+                    const int gc = g / x;   // threads per CTA
+                    // prefer: fits the budget in one CTA (fewest threads), then
+                    // fits over several CTAs (fewest threads), then the
+                    // smallest fragment in one CTA; fewest idle lanes last
+                    const long idle = gc <= 32 ? 32 % gc : (32 - gc % 32) % 32;
+                    long score;
+                    if (ept <= reg_cap && x == 1) score = 300000000L + (4096L - g) * 1000L;
+                    else if (ept <= reg_cap) score = 200000000L + (65536L - g) * 1000L / 16;
+                    else if (x == 1) score = 100000000L - (long)ept * 10L;
+                    else continue;
+                    score -= idle;
+                    if (score > best_score) {
+                        best_score = score;
+                        best[0] = a; best[1] = b; best[2] = c; best[3] = d; best[4] = x;
+                    }
                 }
-    s.ga = best[0]; s.gb = best[1]; s.gc = best[2]; s.gd = best[3];
+    s.ga = best[0]; s.gb = best[1]; s.gc = best[2]; s.gd = best[3]; s.gx = best[4];
+}
+
+// Candidate fragmentations for the autotuner: the current shape first, then
+// G = 1 (register mode) where the class is within twice the register-mode
+// budget, then one shape per group size G (2 <= G <= 256, at most 64
+// elements per thread, the fewest idle lanes), nearest to the current G
+// (in log2 G) first. Shapes whose shared memory exceeds 200 KB are skipped.
+std::vector<KSpec> fragment_candidates(const KSpec &s0, int maxc)
+{
+    std::vector<KSpec> out{s0};
+    const int nf[4] = {ncart(s0.la), ncart(s0.lb), ncart(s0.lc), ncart(s0.ld)};
+    const int ne = nf[0] * nf[1] * nf[2] * nf[3];
+    const int g1_cap = s0.fp32 ? 128 : 64;
+    auto push = [&](int a, int b, int c, int d) {
+        if ((int)out.size() >= maxc) return;
+        for (auto &x : out)
+            if (x.ga == a && x.gb == b && x.gc == c && x.gd == d) return;
+        KSpec s = s0;
+        s.ga = a; s.gb = b; s.gc = c; s.gd = d; s.gx = 1;
+        if (s.smem_bytes() > 200 * 1024) return;
+        out.push_back(s);
+    };
+    if (ne + 3 * s0.ni() <= 2 * g1_cap) push(1, 1, 1, 1);
+    std::map<int, std::array<int, 5>> byg;   // G -> {idle lanes, ga, gb, gc, gd}
+    for (int a = 1; a <= nf[0]; ++a) {
+        if (nf[0] % a) continue;
+        for (int b = 1; b <= nf[1]; ++b) {
+            if (nf[1] % b) continue;
+            for (int c = 1; c <= nf[2]; ++c) {
+                if (nf[2] % c) continue;
+                for (int d = 1; d <= nf[3]; ++d) {
+                    if (nf[3] % d) continue;
+                    const int g = a * b * c * d;
+                    if (g < 2 || g > 256 || ne / g > 64) continue;
+                    const int idle = g <= 32 ? 32 % g : (32 - g % 32) % 32;
+                    auto it = byg.find(g);
+                    if (it == byg.end() || idle < it->second[0]) byg[g] = {idle, a, b, c, d};
+                }
+            }
+        }
+    }
+    std::vector<std::pair<double, int>> ord;
+    const double lg0 = std::log2((double)s0.G());
+    for (auto &kv : byg) ord.push_back({std::fabs(std::log2((double)kv.first) - lg0), kv.first});
+    std::sort(ord.begin(), ord.end());
+    for (auto &o : ord) {
+        const auto &v = byg[o.second];
+        push(v[1], v[2], v[3], v[4]);
+    }
+    return out;
+}
+
+// Tuning table: the fragment shape the autotuner chose per class
+// (angular momenta, primitive counts, tier) and device model, kept in memory
+// and in a text file in the kernel cache directory ("key ga gb gc gd" lines).
+struct TuneTable {
+    std::mutex mu;
+    std::map<std::string, std::map<std::string, std::array<int, 4>>> by_dev;   // by file path
+    std::set<std::string> loaded;
+};
+TuneTable &ttable()
+{
+    static TuneTable t;
+    return t;
+}
+
+std::string tune_key(const KSpec &s)
+{
+    char b[64];
+    snprintf(b, sizeof b, "%d%d%d%d/%d_%d_%d_%d/%d", s.la, s.lb, s.lc, s.ld, s.na, s.nb, s.nc, s.nd, s.fp32);
+    return b;
+}
+
+std::string tune_device(int dev)
+{
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    std::string n;
+    for (const char *c = p.name; *c; ++c) n += (isalnum((unsigned char)*c) ? *c : '_');
+    return n + "_sm" + std::to_string(p.major) + std::to_string(p.minor) + "_" + std::to_string(p.multiProcessorCount);
+}
+
+// JK_TUNING_DIR overrides the directory (default: the kernel cache)
+std::string tune_path(const std::string &devname)
+{
+    const char *e = getenv("JK_TUNING_DIR");
+    std::string d = e && *e ? std::string(e) : cache_dir();
+    if (e && *e) mkdir(d.c_str(), 0755);
+    return d + "/tune_" + devname + ".txt";
+}
+
+// caller holds the table's lock
+void tune_load_locked(TuneTable &t, const std::string &path)
+{
+    if (t.loaded.count(path)) return;
+    t.loaded.insert(path);
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char key[64];
+    int a, b, c, d;
+    while (fscanf(f, "%63s %d %d %d %d", key, &a, &b, &c, &d) == 5) t.by_dev[path][key] = {a, b, c, d};
+    fclose(f);
+}
+
+// Apply a stored shape to s if there is one and it is valid for the class.
+void tune_lookup(int dev, KSpec &s)
+{
+    const std::string path = tune_path(tune_device(dev));
+    TuneTable &t = ttable();
+    std::lock_guard<std::mutex> g(t.mu);
+    tune_load_locked(t, path);
+    auto di = t.by_dev.find(path);
+    if (di == t.by_dev.end()) return;
+    auto it = di->second.find(tune_key(s));
+    if (it == di->second.end()) return;
+    const auto &v = it->second;
+    const int nf[4] = {ncart(s.la), ncart(s.lb), ncart(s.lc), ncart(s.ld)};
+    for (int i = 0; i < 4; ++i)
+        if (v[i] < 1 || nf[i] % v[i]) return;
+    KSpec x = s;
+    x.ga = v[0]; x.gb = v[1]; x.gc = v[2]; x.gd = v[3]; x.gx = 1;
+    if (x.G() > 256 || x.smem_bytes() > 200 * 1024) return;
+    s = x;
+}
+
+void tune_store(int dev, const std::vector<KSpec> &chosen)
+{
+    const std::string path = tune_path(tune_device(dev));
+    TuneTable &t = ttable();
+    std::lock_guard<std::mutex> g(t.mu);
+    tune_load_locked(t, path);
+    auto &m = t.by_dev[path];
+    for (auto &s : chosen) m[tune_key(s)] = {s.ga, s.gb, s.gc, s.gd};
+    const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (auto &kv : m) fprintf(f, "%s %d %d %d %d\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2], kv.second[3]);
+    fclose(f);
+    rename(tmp.c_str(), path.c_str());
 }
 
 // Modelled FLOPs of one contracted quartet of a class (FMA = 2).
@@ -541,7 +720,10 @@ struct jk_handle {
     std::vector<JkPair> h_pairs;
     int num_sms = 0;
     // options
-    double tau32 = 1e-7, router_band = 100.0, pair_cutoff = 1e-18;
+    // tau32: a 16-molecule sweep of the batched workload gave max |dJ| 3e-12,
+    // 3e-10, 3e-9 at 1e-7, 1e-5, 1e-4 (about linear): 1e-4 keeps a 3x margin
+    // to the 1e-8 target
+    double tau32 = 1e-4, router_band = 100.0, pair_cutoff = 1e-18;
     int use_graph = 0, use_dmax = 1, profile = 0;
     int part_index = 0, part_count = 1;    // partitioned builds (multi-GPU split of one batch)
     double prim_eps = 1e-16;               // primitive threshold (never above the cutoff)
@@ -549,6 +731,7 @@ struct jk_handle {
     double init_ms = 0, compile_ms = 0;
     std::vector<cudaEvent_t> prof_ev;      // two per launch slot
     std::vector<jk_launch_prof> prof;
+    std::vector<int> prof_slot;            // launch * 2 + tier of each prof record
     // spherical molecules: Cartesian scratch copies of D, J, K
     std::vector<char> mol_sph;             // per molecule
     std::vector<int> sh_ao_user;           // molecule-local AO offset in the caller's basis
@@ -770,6 +953,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     if ((rc = upload(&d_cp, cp))) return rc;
     struct G2 { JkPair *p; double *q; ~G2() { cudaFree(p); cudaFree(q); } } g2{d_cp, nullptr};
     CK(cudaMalloc(&d_q, sizeof(double) * ncand));
+    CK(cudaMemset(d_q, 0, sizeof(double) * ncand));   // split groups combine by atomic max
     g2.q = d_q;
     {
         // one Schwarz launch per pair class
@@ -800,7 +984,8 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
             a.Qout = d_q + ranges[k].first;
             a.npair = (int)(ranges[k].second - ranges[k].first);
             const long long groups = specs[k].groups_per_cta();
-            unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((a.npair + groups - 1) / groups,
+            const long long units = (long long)a.npair * specs[k].gx;
+            unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((units + groups - 1) / groups,
                                                                                 (long long)h->num_sms * 8));
             void *params[] = {&a};
             CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem, 0,
@@ -850,6 +1035,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
         struct G3 { std::function<void()> f; ~G3() { f(); } } g3{cl2};
         if ((rc = upload(&d_pseudo, pseudo))) return rc;
         CK(cudaMalloc(&d_qp, sizeof(double) * npp));
+        CK(cudaMemset(d_qp, 0, sizeof(double) * npp));
         std::vector<KInfo> ki;
         auto tc = std::chrono::steady_clock::now();
         if ((rc = ensure_kernels(specs, ki))) return rc;
@@ -862,7 +1048,8 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
             a.Qout = d_qp + ranges[k].first;
             a.npair = (int)(ranges[k].second - ranges[k].first);
             const long long groups = specs[k].groups_per_cta();
-            unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((a.npair + groups - 1) / groups,
+            const long long units = (long long)a.npair * specs[k].gx;
+            unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((units + groups - 1) / groups,
                                                                                 (long long)h->num_sms * 8));
             void *params[] = {&a};
             CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem, 0,
@@ -966,6 +1153,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
                 s.na = A.na; s.nb = A.nb; s.nc = B.na; s.nd = B.nb;
                 s.fp32 = t;
                 choose_fragments(s, false);
+                tune_lookup(h->device, s);
             }
             // work items: per bra, ceil(candidates / JK_CHUNK) (at least one), where the
             // candidates are the kets (sorted by Q) with Q_ab Q_cd > JK_ITEM_EPS
@@ -1198,7 +1386,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 3 * nl, s0));
         CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, s0));
         jk_dmax_kernel<<<h->nshell, 128, 0, s0>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
-                                                  h->d_dmax, h->d_dmax_mol);
+                                                  h->d_dmax, h->d_dmax_mol, h->d_err);
         CK(cudaGetLastError());
         ++nlaunch_aux;
         if (nbranch > 1) {
@@ -1249,8 +1437,9 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.log_cap = logs ? logs->cap : 0;
             a.nbra = A.n;
             a.item_prefix = L.d_prefix;
-            a.item_lo = L.nitems * h->part_index / h->part_count;
-            a.item_hi = L.nitems * (h->part_index + 1) / h->part_count;
+            const long long nunits = L.nitems * specs[k].gx;   // work items x slabs
+            a.item_lo = nunits * h->part_index / h->part_count;
+            a.item_hi = nunits * (h->part_index + 1) / h->part_count;
             a.chunk = JK_CHUNK;
             a.prim_eps = std::min(cutoff, h->prim_eps);
             a.omega = std::fabs(h->omega);
@@ -1339,7 +1528,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         int64_t routed_fp32 = 0;
         stats->ms = ms;
         stats->kernel_launches = (int64_t)specs.size() + nlaunch_aux;
-        if (prof) h->prof.clear();
+        if (prof) { h->prof.clear(); h->prof_slot.clear(); }
         for (size_t k = 0; k < specs.size(); ++k) {
             const int slot = lidx[k] * 2 + tier[k];
             unsigned long long nq = cnt[3 * slot], np = cnt[3 * slot + 1];
@@ -1364,28 +1553,50 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                 p.ms = lm;
                 p.flops_model = flops_of(x, ndm, nq, np);
                 h->prof.push_back(p);
+                h->prof_slot.push_back(slot);
             }
         }
         stats->quartets_routed = routed_fp32;
         if (err) {
             CK(cudaMemset(h->d_err, 0, sizeof(int)));
+            if (err & JK_ERR_DEV_NAN) return fail(JK_ERR_NAN, "the density holds NaN or infinite values");
             return fail(err == JK_ERR_DEV_TIMEOUT ? JK_ERR_TIMEOUT : JK_ERR_CUDA, "device error word %d", err);
         }
     }
     return JK_OK;
 }
 
-// Device weights for inference from the FP32 master copy (BF16 rounding).
+// Device weights for inference from the FP32 master copy: BF16 rounding, and
+// the matrices laid out as mma.m16n8k16 B fragments. For k-step ks, n-tile nt
+// and lane (g = lane / 4, t = lane % 4) the two registers hold
+// {W[16ks+2t][n], W[16ks+2t+1][n]} and {W[16ks+2t+8][n], W[16ks+2t+9][n]},
+// n = 8nt + g, low half first.
+static unsigned router_pack(float lo, float hi) { return (unsigned)jk_f2bf(lo) | ((unsigned)jk_f2bf(hi) << 16); }
+
+template <typename W>
+static void router_fragments(W w, int nks, int nnt, unsigned *dst)
+{
+    for (int ks = 0; ks < nks; ++ks)
+        for (int nt = 0; nt < nnt; ++nt)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3, n = nt * 8 + g, k = ks * 16 + 2 * t;
+                unsigned *r = dst + ((size_t)(ks * nnt + nt) * 32 + lane) * 2;
+                r[0] = router_pack(w(k, n), w(k + 1, n));
+                r[1] = router_pack(w(k + 8, n), w(k + 9, n));
+            }
+}
+
 void router_dev_from_blob(const jk_router_blob &w, JkRouterDev &d)
 {
     memset(&d, 0, sizeof d);
     for (int i = 0; i < 16; ++i) { d.mu[i] = w.mu[i]; d.isd[i] = w.isd[i]; }
-    for (int i = 0; i < JK_RT_NINP * JK_RT_NH; ++i) d.W1[i] = jk_f2bf(w.theta[JK_RT_OFF_W1 + i]);
-    for (int i = 0; i < JK_RT_NH; ++i) d.b1[i] = w.theta[JK_RT_OFF_B1 + i];
-    for (int i = 0; i < JK_RT_NH * JK_RT_NH; ++i) d.W2[i] = jk_f2bf(w.theta[JK_RT_OFF_W2 + i]);
-    for (int i = 0; i < JK_RT_NH; ++i) d.b2[i] = w.theta[JK_RT_OFF_B2 + i];
-    for (int i = 0; i < JK_RT_NH; ++i) d.W3[i] = jk_f2bf(w.theta[JK_RT_OFF_W3 + i]);
-    d.b3 = w.theta[JK_RT_OFF_B3];
+    const float *th = w.theta;
+    router_fragments([th](int k, int n) { return th[JK_RT_OFF_W1 + k * JK_RT_NH + n]; }, 1, 8, d.W1p);
+    router_fragments([th](int k, int n) { return th[JK_RT_OFF_W2 + k * JK_RT_NH + n]; }, 4, 8, d.W2p);
+    router_fragments([th](int k, int n) { return n == 0 ? th[JK_RT_OFF_W3 + k] : 0.0f; }, 4, 1, d.W3p);
+    for (int i = 0; i < JK_RT_NH; ++i) d.b1[i] = th[JK_RT_OFF_B1 + i];
+    for (int i = 0; i < JK_RT_NH; ++i) d.b2[i] = th[JK_RT_OFF_B2 + i];
+    d.b3 = th[JK_RT_OFF_B3];
     d.margin = w.margin;
 }
 
@@ -1446,6 +1657,125 @@ int noalloc_scratch(JkNoAllocScratch **out)
 }  // namespace
 
 // ===================================================================== ABI
+// Autotuner (the per-device grid search over fragmentations of Sec. 3.2, run
+// on the caller's own data): every class-pair launch whose estimated share of
+// the work is at least min_share gets up to maxc candidate shapes; round r
+// gives every launch its r-th candidate and runs two serialised, profiled
+// builds (CUDA events around each launch); each launch keeps its fastest
+// candidate. The chosen shapes stay in the handle and go to the tuning table.
+int tune_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int with_k, double cutoff, int mode,
+              double *const *J, double *const *K, void *stream, int maxc, double min_share, jk_tune_report *rep)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    if (maxc < 1 || maxc > 16) return fail(JK_ERR_ARG, "max_candidates must be in 1..16");
+    if (!(min_share >= 0.0 && min_share <= 1.0)) return fail(JK_ERR_ARG, "min_share must be in [0, 1]");
+    if (mode < JK_PREC_FP64 || mode > JK_PREC_FP32) return fail(JK_ERR_ARG, "bad precision_mode %d", mode);
+    if (ndm < 1 || ndm > JK_NDM_MAX) return fail(JK_ERR_ARG, "bad n_dm");
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool two = mode == JK_PREC_MIXED || mode == JK_PREC_MIXED_ROUTED;
+    std::vector<int> tiers;
+    if (mode == JK_PREC_FP64 || two) tiers.push_back(0);
+    if (mode == JK_PREC_FP32 || two) tiers.push_back(1);
+    double total = 0;
+    for (auto &L : h->launches) total += L.cost;
+    struct Item {
+        int l, t;
+        std::vector<KSpec> c;
+        double first = INFINITY, best = INFINITY;
+        int bi = 0;
+    };
+    std::vector<Item> items;
+    for (size_t l = 0; l < h->launches.size(); ++l) {
+        const Launch &L = h->launches[l];
+        if (L.nitems == 0 || L.cost < min_share * total) continue;
+        for (int t : tiers) {
+            Item it;
+            it.l = (int)l;
+            it.t = t;
+            it.c = fragment_candidates(L.spec[t], maxc);
+            if (it.c.size() > 1) items.push_back(it);
+        }
+    }
+    // every candidate compiled (in parallel) and loaded before any timing;
+    // shapes that cannot be resident on an SM are dropped
+    {
+        std::vector<KSpec> all;
+        for (auto &it : items)
+            for (auto c : it.c) {
+                c.ndm = ndm; c.doj = with_j ? 1 : 0; c.dok = with_k ? 1 : 0;
+                c.mode = mode == JK_PREC_MIXED_ROUTED ? 1 : 0;
+                c.op = h->omega == 0.0 ? 0 : (h->omega > 0.0 ? 1 : 2);
+                all.push_back(c);
+            }
+        std::vector<KInfo> ki;
+        int rc = ensure_kernels(all, ki);
+        if (rc) return rc;
+        size_t k = 0;
+        for (auto &it : items) {
+            std::vector<KSpec> keep;
+            for (size_t j = 0; j < it.c.size(); ++j, ++k)
+                if (j == 0 || ki[k].blocks_per_sm >= 1) keep.push_back(it.c[j]);
+            it.c = keep;
+        }
+    }
+    size_t nround = 0;
+    for (auto &it : items) nround = std::max(nround, it.c.size());
+    std::map<int, int> by_slot;
+    for (size_t i = 0; i < items.size(); ++i) by_slot[items[i].l * 2 + items[i].t] = (int)i;
+    const int o_prof = h->profile, o_branches = h->branches, o_graph = h->use_graph;
+    h->profile = 1;
+    h->branches = 1;
+    h->use_graph = 0;
+    int rc = JK_OK;
+    for (size_t r = 0; r < nround && rc == JK_OK; ++r) {
+        for (auto &it : items) h->launches[it.l].spec[it.t] = it.c[std::min(r, it.c.size() - 1)];
+        std::vector<double> tm(items.size(), INFINITY);
+        for (int rep2 = 0; rep2 < 2 && rc == JK_OK; ++rep2) {
+            jk_stats st;
+            rc = build_impl(h, D, ndm, with_j, with_k, cutoff, mode, J, K, stream, &st);
+            if (rc) break;
+            for (size_t p = 0; p < h->prof.size(); ++p) {
+                auto f = by_slot.find(h->prof_slot[p]);
+                if (f != by_slot.end()) tm[f->second] = std::min(tm[f->second], (double)h->prof[p].ms);
+            }
+        }
+        for (size_t i = 0; i < items.size(); ++i) {
+            Item &it = items[i];
+            if (r >= it.c.size()) continue;
+            if (r == 0) it.first = tm[i];
+            if (tm[i] < it.best) { it.best = tm[i]; it.bi = (int)r; }
+        }
+    }
+    h->profile = o_prof;
+    h->branches = o_branches;
+    h->use_graph = o_graph;
+    std::vector<KSpec> chosen;
+    int changed = 0;
+    double before = 0, after = 0;
+    for (auto &it : items) {
+        const int b = rc == JK_OK ? it.bi : 0;
+        h->launches[it.l].spec[it.t] = it.c[b];
+        chosen.push_back(it.c[b]);
+        changed += b != 0;
+        before += it.first;
+        after += it.best;
+    }
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
+    h->graphs.clear();
+    if (rc) return rc;
+    tune_store(h->device, chosen);
+    if (rep) {
+        memset(rep, 0, sizeof(*rep));
+        rep->launches_tuned = (int32_t)items.size();
+        for (auto &it : items) rep->candidates_timed += (int32_t)it.c.size();
+        rep->changed = changed;
+        rep->ms_before = before;
+        rep->ms_after = after;
+        rep->tune_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return JK_OK;
+}
+
 extern "C" {
 
 int jk_router_gradient_noalloc(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
@@ -1660,7 +1990,7 @@ int jk_router_forward(const jk_router_blob *w, const float *X, int64_t n, float 
     JkRouterDev *dd = nullptr;
     CK(cudaMalloc(&dd, sizeof d));
     cudaMemcpy(dd, &d, sizeof d, cudaMemcpyHostToDevice);
-    jk_mlp_forward_kernel<<<(unsigned)((n + 255) / 256), 256>>>(dd, X, (long long)n, y_out);
+    jk_mlp_forward_kernel<<<(unsigned)((n + 127) / 128), 128>>>(dd, X, (long long)n, y_out);
     cudaError_t e = cudaDeviceSynchronize();
     cudaFree(dd);
     if (e != cudaSuccess) return fail(JK_ERR_CUDA, "router forward: %s", cudaGetErrorString(e));
@@ -1916,6 +2246,37 @@ int jk_compile_basis(const jk_shell *shells, int32_t nshell, int32_t n_dm, int32
     } catch (const std::exception &e) {
         return fail(JK_ERR_COMPILE, "host exception: %s", e.what());
     }
+}
+
+int jk_autotune(jk_handle *h, const double *const *D, int32_t n_dm, int with_j, int with_k, double cutoff,
+                int precision_mode, double *const *J, double *const *K, void *stream, int32_t max_candidates,
+                double min_share, jk_tune_report *report)
+{
+    try {
+        return tune_impl(h, D, n_dm, with_j, with_k, cutoff, precision_mode, J, K, stream, max_candidates, min_share,
+                         report);
+    } catch (const std::exception &e) {
+        return fail(JK_ERR_CUDA, "host exception: %s", e.what());
+    }
+}
+
+int jk_fragment_candidates(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t fp32, int32_t max_candidates,
+                           int32_t *frag, int32_t *n)
+{
+    if (la < 0 || lb < 0 || lc < 0 || ld < 0 || la > JK_LMAX || lb > JK_LMAX || lc > JK_LMAX || ld > JK_LMAX)
+        return fail(JK_ERR_UNSUPPORTED, "angular momentum out of range");
+    if (max_candidates < 1 || max_candidates > 16 || !frag || !n) return fail(JK_ERR_ARG, "bad arguments");
+    KSpec s;
+    s.kind = 0;
+    s.la = la; s.lb = lb; s.lc = lc; s.ld = ld;
+    s.fp32 = fp32 ? 1 : 0;
+    choose_fragments(s, false);
+    auto c = fragment_candidates(s, max_candidates);
+    for (size_t i = 0; i < c.size(); ++i) {
+        frag[4 * i] = c[i].ga; frag[4 * i + 1] = c[i].gb; frag[4 * i + 2] = c[i].gc; frag[4 * i + 3] = c[i].gd;
+    }
+    *n = (int32_t)c.size();
+    return JK_OK;
 }
 
 const char *jk_last_error(void) { return g_err.c_str(); }

@@ -186,7 +186,7 @@ struct JkShape {
     // reals of shared memory per group (G > 1): 2D tables and the roots
     static constexpr int SMEM_GROUP = (G == 1) ? 0 : (NRE * 3 * NI + 2 * NRE);
     static_assert(NFA % GA == 0 && NFB % GB == 0 && NFC % GC == 0 && NFD % GD == 0, "fragment");
-    static_assert(G <= 1024, "a group fits one CTA");
+    static_assert(G <= 16 * 1024, "a group fits 16 CTAs");
 };
 
 // Offsets into a 2D table for the components a thread owns (G > 1).
@@ -247,7 +247,10 @@ __device__ __forceinline__ void jk_group_sync(unsigned gmask)
 // ------------------------------------------------ one contracted quartet
 // Accumulates the thread's fragment T[EPT] of the contracted block (ab|cd)
 // over every primitive quartet (eq:rys0). `grp` is the group's shared
-// memory (G > 1), gmask the group's lane mask.
+// memory (G > 1), gmask the group's lane mask. The roots and 2D tables are
+// built by the NT threads that share `grp` (tg < NT: the thread's index
+// among them), the whole group, or, for a group split over several CTAs,
+// the group's threads in this CTA.
 // Root r (< NRE) of the operator: set 0 at T (1/r) or at theta T (erf);
 // for OP 2 set 1 is the erf part with negated weight. Returns u and w * pref.
 template <int NR, int OP, typename R>
@@ -271,7 +274,8 @@ __device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, in
 }
 
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
-          int GA, int GB, int GC, int GD, typename R, int OP = 0>
+          int GA, int GB, int GC, int GD, typename R, int OP = 0,
+          int NT = JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>::G>
 __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, double qthr, double omega,
                                            const typename JkPP<R>::T *__restrict__ pp,
                                            const R *__restrict__ rys, R *grp, unsigned gmask, int tg, bool act,
@@ -339,14 +343,14 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
                 }
             } else {
                 R *roots = grp + NRE * 3 * S::NI;   // [0, NRE): u ; [NRE, 2 NRE): w * pref
-                for (int r = tg; r < NRE; r += S::G) {
+                for (int r = tg; r < NRE && tg < NT; r += NT) {
                     R u, wp;
                     jk_op_root<NR, OP, R>(Tt, rho, pref, omega, r, rys, u, wp);
                     roots[r] = u;
                     roots[NRE + r] = wp;
                 }
                 jk_group_sync<S::G>(gmask);
-                for (int task = tg; task < 3 * NRE; task += S::G) {
+                for (int task = tg; task < 3 * NRE && tg < NT; task += NT) {
                     const int r = task / 3, dir = task - 3 * r;
                     const R u = roots[r];
                     const R b00 = (R)0.5 * u * inv_pq;
@@ -397,18 +401,41 @@ template <> __device__ __forceinline__ const double *jk_rys<double>(const JkClas
 template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassArgs &a) { return a.rys32; }
 
 // ------------------------------------------------- screening of a candidate
+template <int MODE>
+__device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
+                                                const double *dmx, double dmol, int j, int ke, bool &sig,
+                                                bool &stop, bool &band, double &dmq, double &Bout);
 // Keep (bra, ket j) iff lo < Q_ab Q_cd Dmax <= hi; `stop` when even the
 // molecule's largest density element cannot lift this ket (and every later
 // one, kets being sorted by Q) above lo.
 template <int MODE>
 __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkPairFeat &braf,
                                           const JkMol &mol, const double *dmx, double dmol, int j, int ke,
-                                          bool &sig, bool &stop, bool &band, double &dmq)
+                                          bool &sig, bool &stop, bool &band, double &dmq, unsigned short *rsm)
 {
     sig = false;
     stop = false;
     band = false;
     dmq = 1.0;
+    double B = 0.0;
+    jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, j, ke, sig, stop, band, dmq, B);
+    if (MODE == 1) {
+        // learned router for the band candidates, all lanes together on the tensor cores
+        if (__ballot_sync(0xffffffffu, band)) {
+            const JkPairFeat kf = band ? args.ket_feat[j] : braf;
+            const bool to32 = jk_router_to_fp32_warp(args.router, braf, kf, band ? B : 2.0 * args.tau,
+                                                     band ? dmq : 1.0, args.tau, rsm);
+            if (band) sig = (args.tier == 1) ? to32 : !to32;
+        }
+        band = band && sig;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
+                                                const double *dmx, double dmol, int j, int ke, bool &sig,
+                                                bool &stop, bool &band, double &dmq, double &Bout)
+{
     if (j >= ke) return;
     const double bq = bra.Q * args.ket[j].Q;
     if (bq * dmol <= args.lo) { stop = true; return; }
@@ -425,12 +452,9 @@ __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair 
     }
     dmq = dm;
     const double B = bq * dm;
+    Bout = B;
     sig = (B > args.lo) && (B <= args.hi);
-    if (MODE == 1 && sig && B > args.tau && B <= args.band_hi) {
-        const bool to32 = jk_router_to_fp32(args.router, braf, args.ket_feat[j], B, dm, args.tau);
-        sig = (args.tier == 1) ? to32 : !to32;
-        band = sig;
-    }
+    band = MODE == 1 && sig && B > args.tau && B <= args.band_hi;
 }
 
 // Density factor of a quartet (the same lookups as jk_screen).
@@ -608,11 +632,15 @@ __device__ __forceinline__ int jk_item_bra(const JkClassArgs &args, long long t)
 
 // ------------------------------------------------------- the class kernel
 // Persistent: warps (or, for groups of more than 32 threads, whole CTAs)
-// take bra pairs from a global counter until none are left.
+// take work items from a global counter until none are left. A group of
+// more than 256 threads (the largest classes, e.g. (gg|gg)) is split over
+// X CTAs: work item t is slab t % X of quartet item t / X, each CTA builds
+// the roots and 2D tables itself and evaluates the elements of its G / X
+// threads.
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
-          int GA, int GB, int GC, int GD, int NDM, int DOJ, int DOK, typename R, int MODE, int OP>
+          int GA, int GB, int GC, int GD, int X, int NDM, int DOJ, int DOK, typename R, int MODE, int OP>
 __global__ void __launch_bounds__(JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G <= 32 ? 128
-                                  : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G + 31) / 32) * 32)
+                                  : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G / X + 31) / 32) * 32)
 jk_class_kernel(const JkClassArgs args)
 {
     typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP> S;
@@ -623,6 +651,7 @@ jk_class_kernel(const JkClassArgs args)
     const typename JkPP<R>::T *pp = jk_pp<R>(args);
     const R *rys = jk_rys<R>(args);
 
+    static_assert(X == 1 || (G > 32 && G % X == 0), "a split group spans whole CTAs");
     if constexpr (G <= 32) {
         constexpr int NGW = 32 / G;
         const int wib = threadIdx.x >> 5;
@@ -630,6 +659,9 @@ jk_class_kernel(const JkClassArgs args)
         const bool active = gw < NGW;
         const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((active ? gw : 0) * G));
         R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
+        // router scratch, 1 KB per warp (MODE 1)
+        __shared__ __align__(16) unsigned short s_rsm[MODE == 1 ? 4 * 32 * JK_RT_NINP : 2];
+        unsigned short *rsm = s_rsm + (MODE == 1 ? wib * 32 * JK_RT_NINP : 0);
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
@@ -663,7 +695,7 @@ jk_class_kernel(const JkClassArgs args)
             for (int base = kb; base < ke; base += 32) {
                 bool sig, stop, band;
                 double dmq;
-                jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq);
+                jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, rsm);
                 unsigned mask = __ballot_sync(0xffffffffu, sig);
                 nq += __popc(mask);
                 if (MODE == 1) nband += __popc(__ballot_sync(0xffffffffu, band));
@@ -714,24 +746,34 @@ jk_class_kernel(const JkClassArgs args)
             }
         }
     } else {
-        // one group per CTA of round_up(G, 32) threads
+        // one group (or one of its X slabs) per CTA of round_up(G / X, 32) threads
+        constexpr int NTC = G / X;
         __shared__ long long s_item;
         __shared__ double s_dm[32];
         __shared__ unsigned s_mask;
         __shared__ int s_stop;
+        __shared__ __align__(16) unsigned short s_rsm[MODE == 1 ? 32 * JK_RT_NINP : 2];
         const int tg = threadIdx.x;
-        const bool act = tg < G;
+        const bool act = tg < NTC;
         const int tgc = act ? tg : 0;
-        const int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
+        int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
         R *grp = reinterpret_cast<R *>(jk_smem_raw);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
         for (;;) {
             if (threadIdx.x == 0) s_item = args.item_lo + (long long)atomicAdd(args.work, 1ull);
             __syncthreads();
-            const long long t = s_item;
+            const long long tt = s_item;
             __syncthreads();
-            if (t >= args.item_hi) break;
+            if (tt >= args.item_hi) break;
+            const long long t = X == 1 ? tt : tt / X;
+            const int slab = (int)(tt - t * X);
+            if constexpr (X > 1) {
+                // this CTA's share of the group: logical threads slab * NTC + tg
+                const int tgl = slab * NTC + tgc;
+                gd = tgl % GD; gc = (tgl / GD) % GC; gb = (tgl / (GD * GC)) % GB; ga = tgl / (GD * GC * GB);
+                jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
+            }
             const int item = jk_item_bra(args, t);
             const int ch = (int)(t - __ldg(args.item_prefix + item));
             const int nch = (int)(__ldg(args.item_prefix + item + 1) - __ldg(args.item_prefix + item));
@@ -758,7 +800,7 @@ jk_class_kernel(const JkClassArgs args)
                 if (threadIdx.x < 32) {
                     bool sig, stop, band;
                     double dmq;
-                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq);
+                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, s_rsm);
                     s_dm[lane] = dmq;
                     const unsigned msk = __ballot_sync(0xffffffffu, sig);
                     const int anystop = __any_sync(0xffffffffu, stop);
@@ -777,7 +819,7 @@ jk_class_kernel(const JkClassArgs args)
                     R T[S::EPT];
 #pragma unroll
                     for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
-                    const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP>(
+                    const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP, NTC>(
                         bra, ket, args.prim_eps / s_dm[myket - base], args.omega, pp, rys, grp, 0u, tg, act, off, T);
                     nprim += np;
                     if (act) {
@@ -788,7 +830,7 @@ jk_class_kernel(const JkClassArgs args)
                         jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
                                                                      ket.b_ao + gd * FD, jab);
                     }
-                    if (MODE == 2) {
+                    if (MODE == 2 && X == 1) {   // labels need the whole block's max |T|
                         __shared__ double s_tm[32];
                         double tm = 0.0;
                         if (act) {
@@ -813,7 +855,7 @@ jk_class_kernel(const JkClassArgs args)
                 if (stop) break;
             }
             if (DOJ && act) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
-            if (threadIdx.x == 0 && nq) {
+            if (threadIdx.x == 0 && nq && slab == 0) {
                 atomicAdd(args.stats, nq);
                 atomicAdd(args.stats + 1, nprim);
                 if (nband) atomicAdd(args.stats + 2, nband);
@@ -825,13 +867,17 @@ jk_class_kernel(const JkClassArgs args)
 // ------------------------------------------------- Schwarz factors Q_ab
 // Diagonal quartets (ab|ab) of one pair class in FP64; Q_ab is the square
 // root of the largest |(mu nu|mu nu)| (eq:schwartz at shell level).
-template <int LA, int LB, int NPA, int NPB, int GA, int GB, int GC, int GD>
+// A group of more than 1024 threads is split over X CTAs (slab t % X of
+// pair t / X); the CTAs combine their maxima by an atomic max on Qout, which
+// the caller zeroes.
+template <int LA, int LB, int NPA, int NPB, int GA, int GB, int GC, int GD, int X>
 __global__ void __launch_bounds__(JkShape<LA, LB, LA, LB, GA, GB, GC, GD>::G <= 32 ? 128
-                                  : ((JkShape<LA, LB, LA, LB, GA, GB, GC, GD>::G + 31) / 32) * 32)
+                                  : ((JkShape<LA, LB, LA, LB, GA, GB, GC, GD>::G / X + 31) / 32) * 32)
 jk_schwarz_kernel(const JkSchwarzArgs args)
 {
     typedef JkShape<LA, LB, LA, LB, GA, GB, GC, GD> S;
     static_assert(GA == GC && GB == GD, "diagonal elements must stay inside one thread");
+    static_assert(X == 1 || (S::G > 32 && S::G % X == 0), "a split group spans whole CTAs");
     constexpr int G = S::G;
     constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
     extern __shared__ double jk_smem_raw[];
@@ -872,20 +918,28 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
             __syncwarp();
         }
     } else {
+        constexpr int NTC = G / X;
         __shared__ double s_max[32];
         const int tg = threadIdx.x;
-        const bool act = tg < G;
+        const bool act = tg < NTC;
         const int tgc = act ? tg : 0;
-        const int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
+        int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
         double *grp = jk_smem_raw;
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
-        for (int pi = blockIdx.x; pi < args.npair; pi += gridDim.x) {
+        for (long long t = blockIdx.x; t < (long long)args.npair * X; t += gridDim.x) {
+            const int pi = (int)(t / X), slab = (int)(t - (long long)pi * X);
+            if constexpr (X > 1) {
+                const int tgl = slab * NTC + tgc;
+                gd = tgl % GD; gc = (tgl / GD) % GC; gb = (tgl / (GD * GC)) % GB; ga = tgl / (GD * GC * GB);
+                jk_make_offsets<LA, LB, LA, LB, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
+            }
             const JkPair pr = args.pairs[pi];
             double T[S::EPT];
 #pragma unroll
             for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, 0.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
+            jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double, 0, NTC>(
+                pr, pr, -1.0, 0.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
             double mx = 0.0;
             if (act && ga == gc && gb == gd) {
 #pragma unroll
@@ -900,7 +954,10 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
             if (threadIdx.x == 0) {
                 double m2 = 0.0;
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, s_max[w]);
-                args.Qout[pi] = sqrt(m2);
+                // non-negative doubles order like their bit patterns
+                if (X == 1) args.Qout[pi] = sqrt(m2);
+                else atomicMax(reinterpret_cast<unsigned long long *>(args.Qout + pi),
+                               (unsigned long long)__double_as_longlong(sqrt(m2)));
             }
             __syncthreads();
         }

@@ -1,32 +1,36 @@
 // Learned precision router: a 12 -> 64 -> 64 -> 1 MLP with BF16 weights and
 // FP32 accumulation that predicts, for a shell quartet inside the band
-// tau32 < Q_ab Q_cd Dmax <= K tau32, y = log10(max|T| Dmax / (Q_ab Q_cd Dmax)),
-// i.e. how far the quartet's largest integral times density sits below its
-// Schwarz bound. The quartet runs in FP32 iff log10(B / tau32) + y <= 0. The
-// rigorous bound still caps every routed quartet at K tau32.
+// tau32 < Q_ab Q_cd Dmax <= K tau32, y = log10(max|T| / (Q_ab Q_cd)), i.e.
+// how far the quartet's largest integral sits below its Schwarz bound. The
+// quartet runs in FP32 iff log10(B / tau32) + y + margin <= 0. The rigorous
+// bound still caps every routed quartet at K tau32.
 //
-// This header is compiled twice: into the runtime-compiled integral kernels
-// (routing decisions) and into the library's training kernels. Every
-// floating-point step uses an explicitly rounded intrinsic so that the FP64
-// and FP32 integral kernels, compiled separately, reach bit-identical
-// decisions for the same quartet (a quartet must land in exactly one tier).
+// Inference runs on the tensor cores, one warp at a time: the 32 candidates
+// a screening warp holds are the rows of mma.sync.m16n8k16 (BF16 inputs,
+// FP32 accumulation), 88 MMAs per warp for the three layers. The inputs of
+// each layer (normalised features, hidden activations) are rounded to BF16;
+// the training kernels and the CPU reference round the same way.
+//
+// This header is compiled into the runtime-compiled integral kernels (both
+// tiers) and into the library's training kernels. Every step is either an
+// MMA (fixed accumulation order) or an explicitly rounded intrinsic, so the
+// FP64 and FP32 tier kernels reach bit-identical decisions for a quartet.
 #pragma once
 
 #define JK_RT_NIN 12
 #define JK_RT_NINP 16   // inputs padded
 #define JK_RT_NH 64
 
-// Device-side weights (built on the host from the FP32 master copy).
+// Device-side weights, built on the host from the FP32 master copy. The
+// weight matrices are stored in the B-fragment order of mma.m16n8k16
+// (per k-step, n-tile, lane: two 32-bit registers of two BF16 values each).
 struct JkRouterDev {
-    float mu[JK_RT_NINP], isd[JK_RT_NINP];               // feature normalisation
-    unsigned short W1[JK_RT_NINP * JK_RT_NH];            // bf16, [in][hidden]
-    float b1[JK_RT_NH];
-    unsigned short W2[JK_RT_NH * JK_RT_NH];              // bf16, [in][out]
-    float b2[JK_RT_NH];
-    unsigned short W3[JK_RT_NH];                         // bf16
-    float b3;
-    float margin;                                        // added to the prediction (safety)
-    float pad[2];
+    float mu[JK_RT_NINP], isd[JK_RT_NINP];   // feature normalisation
+    float b1[JK_RT_NH], b2[JK_RT_NH];
+    float b3, margin, pad[2];
+    unsigned W1p[1 * 8 * 32 * 2];            // 16 x 64
+    unsigned W2p[4 * 8 * 32 * 2];            // 64 x 64
+    unsigned W3p[4 * 1 * 32 * 2];            // 64 x 8 (column 0 used)
 };
 
 // Per shell pair, for the features (host-computed at init).
@@ -38,7 +42,26 @@ struct JkPairFeat {
     float lsum;           // l_a + l_b
 };
 
-__device__ __forceinline__ float jk_bf16f(unsigned short w) { return __uint_as_float(((unsigned)w) << 16); }
+// float -> bf16 bits, round to nearest even (integer arithmetic only)
+__device__ __forceinline__ unsigned jk_bf16_bits(float f)
+{
+    unsigned u = __float_as_uint(f);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u >> 16;
+    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ unsigned jk_pack_bf16(float lo, float hi)
+{
+    return jk_bf16_bits(lo) | (jk_bf16_bits(hi) << 16);
+}
+
+__device__ __forceinline__ void jk_mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 // Features of quartet (ab|cd) with bound B and density factor dmax.
 __device__ __forceinline__ void jk_router_features(const JkPairFeat &fa, const JkPairFeat &fc, double B,
@@ -61,37 +84,91 @@ __device__ __forceinline__ void jk_router_features(const JkPairFeat &fa, const J
     x[11] = (float)log10(B / tau);
 }
 
-// Prediction y (log10 units) for one feature vector.
-__device__ __forceinline__ float jk_router_eval(const JkRouterDev *__restrict__ R, const float x[JK_RT_NIN])
+// Prediction (margin included) for the candidate this lane holds; every lane
+// of the warp must call it (warp-synchronous). sm: 32 x 16 BF16 scratch of
+// this warp in shared memory.
+__device__ __forceinline__ float jk_router_warp(const JkRouterDev *__restrict__ R, const float x[JK_RT_NIN],
+                                                unsigned short *sm)
 {
-    float xn[JK_RT_NIN];
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    // normalised features of this lane's candidate -> BF16 row `lane`
 #pragma unroll
-    for (int i = 0; i < JK_RT_NIN; ++i) xn[i] = __fmul_rn(__fadd_rn(x[i], -__ldg(&R->mu[i])), __ldg(&R->isd[i]));
-    float h1[JK_RT_NH];
-#pragma unroll 4
-    for (int o = 0; o < JK_RT_NH; ++o) {
-        float acc = __ldg(&R->b1[o]);
-#pragma unroll
-        for (int i = 0; i < JK_RT_NIN; ++i) acc = __fmaf_rn(xn[i], jk_bf16f(__ldg(&R->W1[i * JK_RT_NH + o])), acc);
-        h1[o] = fmaxf(acc, 0.0f);
+    for (int i = 0; i < JK_RT_NINP; ++i) {
+        const float v = i < JK_RT_NIN ? __fmul_rn(__fadd_rn(x[i], -__ldg(&R->mu[i])), __ldg(&R->isd[i])) : 0.0f;
+        sm[lane * JK_RT_NINP + i] = (unsigned short)jk_bf16_bits(v);
     }
-    float y = __ldg(&R->b3);
-#pragma unroll 2
-    for (int o = 0; o < JK_RT_NH; ++o) {
-        float acc = __ldg(&R->b2[o]);
+    __syncwarp();
+    const unsigned *smw = reinterpret_cast<const unsigned *>(sm);
+    float out[2][4];
 #pragma unroll
-        for (int i = 0; i < JK_RT_NH; ++i) acc = __fmaf_rn(h1[i], jk_bf16f(__ldg(&R->W2[i * JK_RT_NH + o])), acc);
-        y = __fmaf_rn(fmaxf(acc, 0.0f), jk_bf16f(__ldg(&R->W3[o])), y);
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = mt * 16 + g, r1 = r0 + 8;
+        unsigned a[4];
+        a[0] = smw[(r0 * JK_RT_NINP + 2 * t) >> 1];
+        a[1] = smw[(r1 * JK_RT_NINP + 2 * t) >> 1];
+        a[2] = smw[(r0 * JK_RT_NINP + 2 * t + 8) >> 1];
+        a[3] = smw[(r1 * JK_RT_NINP + 2 * t + 8) >> 1];
+        // layer 1: 16 -> 64, bias in the accumulator, ReLU, BF16 -> A of layer 2
+        unsigned h1[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4];
+            c[0] = c[2] = __ldg(&R->b1[nt * 8 + 2 * t]);
+            c[1] = c[3] = __ldg(&R->b1[nt * 8 + 2 * t + 1]);
+            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R->W1p) + nt * 32 + lane);
+            jk_mma_bf16(c, a, b.x, b.y);
+            const int ks = nt >> 1, half = nt & 1;
+            h1[ks][half * 2 + 0] = jk_pack_bf16(fmaxf(c[0], 0.0f), fmaxf(c[1], 0.0f));
+            h1[ks][half * 2 + 1] = jk_pack_bf16(fmaxf(c[2], 0.0f), fmaxf(c[3], 0.0f));
+        }
+        // A fragments of layer 2 for k-step ks: {rows g: cols 2t..} = h1[ks][0],
+        // {g+8} = h1[ks][1], {g, +8 cols} = h1[ks][2], {g+8, +8} = h1[ks][3]
+        unsigned h2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4];
+            c[0] = c[2] = __ldg(&R->b2[nt * 8 + 2 * t]);
+            c[1] = c[3] = __ldg(&R->b2[nt * 8 + 2 * t + 1]);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const unsigned a2[4] = {h1[ks][0], h1[ks][1], h1[ks][2], h1[ks][3]};
+                const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R->W2p) + (ks * 8 + nt) * 32 + lane);
+                jk_mma_bf16(c, a2, b.x, b.y);
+            }
+            const int ks = nt >> 1, half = nt & 1;
+            h2[ks][half * 2 + 0] = jk_pack_bf16(fmaxf(c[0], 0.0f), fmaxf(c[1], 0.0f));
+            h2[ks][half * 2 + 1] = jk_pack_bf16(fmaxf(c[2], 0.0f), fmaxf(c[3], 0.0f));
+        }
+        // layer 3: 64 -> 1 (an 8-wide n-tile, column 0 used)
+        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            const unsigned a3[4] = {h2[ks][0], h2[ks][1], h2[ks][2], h2[ks][3]};
+            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R->W3p) + ks * 32 + lane);
+            jk_mma_bf16(c, a3, b.x, b.y);
+        }
+        out[mt][0] = c[0];
+        out[mt][1] = c[2];
     }
-    return __fadd_rn(y, __ldg(&R->margin));
+    __syncwarp();
+    // row r of tile mt sits in lane 4 (r % 8), register c0 (r < 8) or c2
+    const int mt = lane >> 4, rr = lane & 15, src = 4 * (rr & 7);
+    const float v00 = __shfl_sync(0xffffffffu, out[0][0], src);
+    const float v01 = __shfl_sync(0xffffffffu, out[0][1], src);
+    const float v10 = __shfl_sync(0xffffffffu, out[1][0], src);
+    const float v11 = __shfl_sync(0xffffffffu, out[1][1], src);
+    const float y = mt == 0 ? (rr < 8 ? v00 : v01) : (rr < 8 ? v10 : v11);
+    return __fadd_rn(__fadd_rn(y, __ldg(&R->b3)), __ldg(&R->margin));
 }
 
-// FP32 route decision for a band quartet.
-__device__ __forceinline__ bool jk_router_to_fp32(const JkRouterDev *__restrict__ R, const JkPairFeat &fa,
-                                                  const JkPairFeat &fc, double B, double dmax, double tau)
+// FP32 route decisions for the band candidates of a warp (warp-synchronous).
+__device__ __forceinline__ bool jk_router_to_fp32_warp(const JkRouterDev *__restrict__ R, const JkPairFeat &fa,
+                                                       const JkPairFeat &fc, double B, double dmax, double tau,
+                                                       unsigned short *sm)
 {
     float x[JK_RT_NIN];
     jk_router_features(fa, fc, B, dmax, tau, x);
-    const float y = jk_router_eval(R, x);
+    const float y = jk_router_warp(R, x, sm);
     return __fadd_rn(x[11], y) <= 0.0f;
 }

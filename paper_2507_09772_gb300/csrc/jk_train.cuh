@@ -1,8 +1,10 @@
 // Training kernels of the learned precision router (compiled by nvcc into the
 // library). Parameters theta (FP32 master copy), flat:
 //   W1[16][64] b1[64] W2[64][64] b2[64] W3[64] b3      (5,313 values)
-// The forward pass rounds every weight to BF16 (round to nearest even) and
-// accumulates in FP32, as the inference in the integral kernels does. The
+// The forward pass rounds every weight and every layer input (normalised
+// features, hidden activations) to BF16 (round to nearest even) and
+// accumulates in FP32, as the tensor-core inference in the integral kernels
+// does; the backward pass treats each rounding as the identity. The
 // loss is the pinball (quantile) loss, which biases the prediction upwards so
 // that a quartet is sent to FP32 only when its largest integral is confidently
 // small.
@@ -67,13 +69,14 @@ __global__ void jk_mlp_grad_kernel(const float *__restrict__ theta, const float 
         long long row = idx ? idx[t] : (long long)(jk_mix64(seed * 0x100000001b3ull + (unsigned long long)t) % (unsigned long long)n);
         float xn[JK_RT_NINP];
         for (int i = 0; i < JK_RT_NINP; ++i) xn[i] = 0.0f;
-        for (int i = 0; i < JK_RT_NIN; ++i) xn[i] = (X[row * JK_RT_NIN + i] - mu[i]) * isd[i];
+        for (int i = 0; i < JK_RT_NIN; ++i)
+            xn[i] = jk_bf2f(jk_f2bf(__fmul_rn(__fadd_rn(X[row * JK_RT_NIN + i], -mu[i]), isd[i])));
         float a1[JK_RT_NH], h1[JK_RT_NH];
         for (int o = 0; o < JK_RT_NH; ++o) {
             float acc = sw[JK_RT_OFF_B1 + o];
             for (int i = 0; i < JK_RT_NIN; ++i) acc = fmaf(xn[i], sw[JK_RT_OFF_W1 + i * JK_RT_NH + o], acc);
             a1[o] = acc;
-            h1[o] = fmaxf(acc, 0.0f);
+            h1[o] = jk_bf2f(jk_f2bf(fmaxf(acc, 0.0f)));
         }
         float a2[JK_RT_NH];
         float out = sw[JK_RT_OFF_B3];
@@ -81,7 +84,7 @@ __global__ void jk_mlp_grad_kernel(const float *__restrict__ theta, const float 
             float acc = sw[JK_RT_OFF_B2 + o];
             for (int i = 0; i < JK_RT_NH; ++i) acc = fmaf(h1[i], sw[JK_RT_OFF_W2 + i * JK_RT_NH + o], acc);
             a2[o] = acc;
-            out = fmaf(fmaxf(acc, 0.0f), sw[JK_RT_OFF_W3 + o], out);
+            out = fmaf(jk_bf2f(jk_f2bf(fmaxf(acc, 0.0f))), sw[JK_RT_OFF_W3 + o], out);
         }
         const float u = y[row] - out;                 // pinball: u (q - [u < 0])
         lsum = (double)(u >= 0.0f ? q * u : (q - 1.0f) * u);
@@ -91,7 +94,7 @@ __global__ void jk_mlp_grad_kernel(const float *__restrict__ theta, const float 
         float dh1[JK_RT_NH];
         for (int i = 0; i < JK_RT_NH; ++i) dh1[i] = 0.0f;
         for (int o = 0; o < JK_RT_NH; ++o) {
-            atomicAdd(&sg[JK_RT_OFF_W3 + o], gs * fmaxf(a2[o], 0.0f));
+            atomicAdd(&sg[JK_RT_OFF_W3 + o], gs * jk_bf2f(jk_f2bf(fmaxf(a2[o], 0.0f))));
             if (a2[o] > 0.0f) {
                 const float d2 = gs * sw[JK_RT_OFF_W3 + o];
                 atomicAdd(&sg[JK_RT_OFF_B2 + o], d2);
@@ -133,13 +136,16 @@ __global__ void jk_adam_kernel(float *__restrict__ theta, const float *__restric
 }
 
 // Inference over a batch of feature rows with the device weights (the same
-// function the integral kernels call).
-__global__ void jk_mlp_forward_kernel(const JkRouterDev *__restrict__ R, const float *__restrict__ X, long long n,
-                                      float *__restrict__ out)
+// warp-level tensor-core function the integral kernels call). Blocks of 128
+// threads; rows past n are evaluated on zero features and not stored.
+__global__ void __launch_bounds__(128) jk_mlp_forward_kernel(const JkRouterDev *__restrict__ R,
+                                                             const float *__restrict__ X, long long n,
+                                                             float *__restrict__ out)
 {
+    __shared__ __align__(16) unsigned short s_rsm[4 * 32 * JK_RT_NINP];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
     float x[JK_RT_NIN];
-    for (int i = 0; i < JK_RT_NIN; ++i) x[i] = X[t * JK_RT_NIN + i];
-    out[t] = jk_router_eval(R, x);
+    for (int i = 0; i < JK_RT_NIN; ++i) x[i] = t < n ? X[t * JK_RT_NIN + i] : 0.0f;
+    const float y = jk_router_warp(R, x, s_rsm + (threadIdx.x >> 5) * 32 * JK_RT_NINP);
+    if (t < n) out[t] = y;
 }

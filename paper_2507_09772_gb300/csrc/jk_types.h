@@ -103,3 +103,4 @@ struct JkSchwarzArgs {
 
 #define JK_ERR_DEV_TIMEOUT 1
 #define JK_ERR_DEV_BOUNDS 2
+#define JK_ERR_DEV_NAN 4

@@ -53,7 +53,7 @@ __global__ void jk_pairdata_kernel(int npair, const int *__restrict__ pa, const 
 __global__ void jk_dmax_kernel(const JkMol *__restrict__ mols, const int *__restrict__ sh_mol,
                                const int *__restrict__ mol_sh0, const int *__restrict__ sh_ao,
                                const int *__restrict__ sh_nc, int ndm, double *__restrict__ dmax,
-                               unsigned long long *__restrict__ dmax_mol)
+                               unsigned long long *__restrict__ dmax_mol, int *__restrict__ err)
 {
     const int s = blockIdx.x;
     const int m = sh_mol[s];
@@ -66,10 +66,15 @@ __global__ void jk_dmax_kernel(const JkMol *__restrict__ mols, const int *__rest
         const int sb = mol_sh0[m] + b;
         const int nb = sh_nc[sb], aob = sh_ao[sb];
         double mx = 0.0;
+        bool bad = false;
         for (int k = 0; k < ndm; ++k)
             for (int i = 0; i < na; ++i)
-                for (int j = 0; j < nb; ++j)
-                    mx = fmax(mx, fabs(mol.D[k * nn + (long long)(aoa + i) * mol.nao + aob + j]));
+                for (int j = 0; j < nb; ++j) {
+                    const double v = fabs(mol.D[k * nn + (long long)(aoa + i) * mol.nao + aob + j]);
+                    bad = bad || !(v <= 1.7976931348623157e308);   // NaN or infinity
+                    mx = fmax(mx, v);
+                }
+        if (bad) atomicOr(err, JK_ERR_DEV_NAN);
         dmax[mol.dmax_off + (long long)a * mol.nsh + b] = mx;
         rowmax = fmax(rowmax, mx);
     }

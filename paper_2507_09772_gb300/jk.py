@@ -27,7 +27,8 @@ EXPORTED = ["jk_init", "jk_init_batch", "jk_build", "jk_build_batch", "jk_set_op
             "jk_get_option", "jk_info", "jk_schwarz", "jk_destroy", "jk_router_collect", "jk_router_train",
             "jk_router_forward", "jk_router_gradient", "jk_router_gradient_noalloc", "jk_router_load",
             "jk_profile", "jk_measure_peak",
-            "jk_compile_class", "jk_compile_basis", "jk_last_error"]
+            "jk_compile_class", "jk_compile_basis", "jk_autotune", "jk_fragment_candidates",
+            "jk_last_error"]
 
 ROUTER_NIN = 12
 ROUTER_NPARAM = 5313
@@ -95,6 +96,15 @@ class JkTrainStats(ctypes.Structure):
 _lib = None
 
 
+class JkTuneReport(ctypes.Structure):
+    _fields_ = [("launches_tuned", ctypes.c_int32), ("candidates_timed", ctypes.c_int32),
+                ("changed", ctypes.c_int32), ("pad", ctypes.c_int32), ("ms_before", ctypes.c_double),
+                ("ms_after", ctypes.c_double), ("tune_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 def load_library() -> ctypes.CDLL:
     """Load libjk.so; raises if it has not been built."""
     global _lib
@@ -132,6 +142,9 @@ def load_library() -> ctypes.CDLL:
     lib.jk_router_gradient_noalloc.argtypes = [P(JkRouterBlob), vp, vp, ctypes.c_int64, ctypes.c_float,
                                                P(ctypes.c_float), P(ctypes.c_double), vp]
     lib.jk_measure_peak.argtypes = [i32, ctypes.c_double, dp]
+    lib.jk_autotune.argtypes = [vp, P(vp), i32, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                P(vp), P(vp), vp, i32, ctypes.c_double, P(JkTuneReport)]
+    lib.jk_fragment_candidates.argtypes = [i32, i32, i32, i32, i32, i32, P(i32), P(i32)]
     lib.jk_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name != "jk_last_error":
@@ -332,6 +345,31 @@ def jk_compile_class(la, lb, lc, ld, na, nb, nc, nd, n_dm=1, with_j=1, with_k=1,
 
 
 # ------------------------------------------------------------ convenience
+def jk_autotune(h, Ds: Sequence, n_dm, with_j, with_k, cutoff, precision_mode, Js, Ks, stream=None,
+                max_candidates=4, min_share=0.005) -> dict:
+    """Fragment-shape autotuning on the given densities (J/K are scratch)."""
+    lib = load_library()
+    n = len(Ds)
+    arr = ctypes.c_void_p * n
+    d = arr(*[_ptr(x) for x in Ds])
+    j = arr(*[_ptr(x) for x in Js]) if Js is not None else None
+    k = arr(*[_ptr(x) for x in Ks]) if Ks is not None else None
+    rep = JkTuneReport()
+    _check(lib.jk_autotune(h, d, int(n_dm), int(bool(with_j)), int(bool(with_k)), float(cutoff),
+                           int(precision_mode), j, k, _stream_ptr(stream), int(max_candidates),
+                           float(min_share), ctypes.byref(rep)))
+    return rep.as_dict()
+
+
+def jk_fragment_candidates(la, lb, lc, ld, fp32=0, max_candidates=8):
+    """Candidate fragment shapes [(ga, gb, gc, gd), ...] for a class (no GPU needed)."""
+    lib = load_library()
+    buf = (ctypes.c_int32 * (4 * max_candidates))()
+    n = ctypes.c_int32()
+    _check(lib.jk_fragment_candidates(la, lb, lc, ld, fp32, max_candidates, buf, ctypes.byref(n)))
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
+
+
 class JK:
     """Owns a handle for one molecule or a batch of molecules.
 
@@ -398,6 +436,18 @@ class JK:
         st = jk_build_batch(self.h, Dl, ndm, with_j, with_k, cutoff, mode,
                             J if with_j else None, K if with_k else None, stream, stats)
         return J, K, st
+
+    def autotune(self, D, with_j=True, with_k=True, cutoff=1e-13, precision="fp64", max_candidates=4,
+                 min_share=0.005, stream=None):
+        """Autotune the fragment shapes on these densities (jk_autotune)."""
+        import torch
+        mode = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        Dl = list(D) if isinstance(D, (list, tuple)) else [D]
+        Dl = [d if d.dim() == 3 else d.unsqueeze(0) for d in Dl]
+        Js = [torch.empty_like(d) for d in Dl] if with_j else None
+        Ks = [torch.empty_like(d) for d in Dl] if with_k else None
+        return jk_autotune(self.h, Dl, Dl[0].shape[0], with_j, with_k, cutoff, mode, Js, Ks, stream,
+                           max_candidates, min_share)
 
     def close(self):
         if getattr(self, "h", None) is not None:

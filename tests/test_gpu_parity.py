@@ -342,7 +342,7 @@ def test_incremental_density_build_screens_on_the_change():
     J(D2) = J(D1) + J(D2 - D1), the increment screened by |D2 - D1|."""
     mol = synth.batched_molecule(10, natm=12)
     rng = np.random.default_rng(4)
-    X = rng.standard_normal((mol.nao, mol.nao)) * 1e-4
+    X = rng.standard_normal((mol.nao, mol.nao)) * 1e-8   # a late-SCF-sized change
     D1 = mol.D
     D2 = D1 + (X + X.T)[None]
     J1, K1, s1 = gpu_jk(mol, D=D1, cutoff=1e-13)
@@ -350,7 +350,9 @@ def test_incremental_density_build_screens_on_the_change():
     J2, K2, s2 = gpu_jk(mol, D=D2, cutoff=1e-13)
     assert np.abs(J1 + Jd - J2).max() <= 1e-10
     assert np.abs(K1 + Kd - K2).max() <= 1e-10
-    assert sd["quartets_fp64"] < 0.8 * s2["quartets_fp64"]
+    # a random density does not decay with distance, so most of the 12-atom
+    # molecule's quartets stay above 1e-13 even at |Delta D| ~ 1e-8
+    assert sd["quartets_fp64"] < 0.75 * s2["quartets_fp64"]
 
 
 def test_separate_j_and_k_builds_screen_on_their_own_blocks():
@@ -363,3 +365,85 @@ def test_separate_j_and_k_builds_screen_on_their_own_blocks():
     assert np.abs(J - Jr).max() <= TOL64
     Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13, with_j=False)
     assert np.abs(K - Kr).max() <= TOL64
+
+
+def test_non_finite_density_is_reported_and_the_handle_recovers():
+    mol = synth.tiny_631gs()
+    eng = jk.JK(mol)
+    D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+    Dbad = D.clone()
+    Dbad[0, 3, 5] = float("nan")
+    with pytest.raises(jk.JKError) as e:
+        eng.build(Dbad, stats=True)
+    assert e.value.code == jk.JK_ERR_NAN
+    J, K, _ = eng.build(D, stats=True)
+    torch.cuda.synchronize()
+    eng.close()
+    Jr, Kr, _ = oracle.jk(mol)
+    assert maxdiff(J.cpu().numpy(), Jr) <= TOL64
+
+
+def test_autotune_keeps_results_and_writes_its_table(tmp_path, monkeypatch):
+    """The autotuner times several fragment shapes per launch; whichever it
+    keeps, the build still matches the oracle, and a new handle on the same
+    device reads the chosen shapes back from the tuning table."""
+    monkeypatch.setenv("JK_TUNING_DIR", str(tmp_path))
+    mol = synth.random_small_molecule(7, natm=3, lmax=2, max_nprim=3)
+    eng = jk.JK(mol)
+    try:
+        Dt = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+        rep = eng.autotune(Dt, cutoff=1e-13, max_candidates=3, min_share=0.0)
+        assert rep["launches_tuned"] >= 1
+        assert rep["candidates_timed"] >= 2 * rep["launches_tuned"]
+        assert 0 <= rep["changed"] <= rep["launches_tuned"]
+        assert rep["ms_after"] <= rep["ms_before"] + 1e-9
+        J, K, _ = eng.build(Dt, cutoff=1e-13, stats=True)
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    check(mol, J.cpu().numpy(), Jr, TOL64, "J")
+    check(mol, K.cpu().numpy(), Kr, TOL64, "K")
+    tables = list(tmp_path.glob("tune_*.txt"))
+    assert len(tables) == 1
+    lines = tables[0].read_text().split("\n")
+    assert len([x for x in lines if x.strip()]) == rep["launches_tuned"]
+    # a second handle starts from the stored shapes and still matches
+    J2, K2, _ = gpu_jk(mol, cutoff=1e-13)
+    check(mol, J2, Jr, TOL64, "J (tuned shapes from the table)")
+    check(mol, K2, Kr, TOL64, "K (tuned shapes from the table)")
+
+
+def _g_molecule(spherical):
+    rng = np.random.default_rng(44)
+    xyz = np.array([[0.0, 0.0, 0.0], [1.3, -0.2, 0.5]])
+    per_atom = [[(0, [3.1, 0.45]), (1, [0.8]), (4, [1.1])],
+                [(0, [0.6]), (2, [0.9]), (4, [0.7])]]
+    return synth.custom_basis_molecule(xyz, per_atom, rng, spherical=spherical, name="g-pair")
+
+
+@pytest.mark.parametrize("spherical", [False, True])
+def test_g_shells(spherical):
+    """g shells (l = 4, up to 9 Rys roots). The (gg|gg), (gg|gd), ... classes
+    need more threads per quartet than one CTA holds within the per-thread
+    fragment budget, so each quartet is split over several CTAs; the
+    Schwarz kernel of the gg pairs is split the same way."""
+    mol = _g_molecule(spherical)
+    eng = jk.JK(mol)
+    Q = jk.jk_schwarz(eng.h)
+    eng.close()
+    Qr = oracle.schwarz(mol)
+    kept = Qr > 1e-18
+    assert np.allclose(Q[kept], Qr[kept], rtol=1e-12, atol=0)
+    J, K, _ = gpu_jk(mol, cutoff=1e-13)
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    check(mol, J, Jr, TOL64, "J")
+    check(mol, K, Kr, TOL64, "K")
+
+
+def test_g_shells_mixed_precision():
+    mol = _g_molecule(False)
+    J, K, st = gpu_jk(mol, cutoff=1e-13, precision="mixed")
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    check(mol, J, Jr, TOL_MIXED, "J")
+    check(mol, K, Kr, TOL_MIXED, "K")

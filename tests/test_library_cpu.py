@@ -90,3 +90,33 @@ def test_compile_basis_builds_every_kernel_of_a_basis(lib, tmp_path, monkeypatch
     # 3 pair classes: 2 Schwarz kernels each (contracted, primitive) + 6 class pairs
     assert nk == 3 * 2 + 6
     assert len(list(tmp_path.iterdir())) == nk
+
+
+def _ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+@pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 1, 0), (2, 2, 2, 2), (3, 2, 3, 2),
+                                 (3, 3, 3, 3), (4, 4, 2, 2)])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_fragment_candidates_are_valid_shapes(lib, cls, fp32):
+    """Autotuner candidates: distinct shapes, each g dividing its shell's
+    Cartesian size, G <= 256 and at most 64 elements per thread (G = 1 and the
+    built-in heuristic's shape excepted, which come first)."""
+    c = jk.jk_fragment_candidates(*cls, fp32=fp32, max_candidates=8)
+    assert 1 <= len(c) <= 8 and len(set(c)) == len(c)
+    nf = [_ncart(l) for l in cls]
+    ne = int(np.prod(nf))
+    for k, g in enumerate(c):
+        assert all(n % x == 0 for n, x in zip(nf, g)), g
+        G = int(np.prod(g))
+        assert G <= 256
+        if k > 0 and G > 1:
+            assert ne // G <= 64
+
+
+def test_fragment_candidates_reject_bad_arguments(lib):
+    with pytest.raises(jk.JKError):
+        jk.jk_fragment_candidates(5, 0, 0, 0)
+    with pytest.raises(jk.JKError):
+        jk.jk_fragment_candidates(1, 1, 1, 1, max_candidates=0)

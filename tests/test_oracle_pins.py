@@ -96,7 +96,7 @@ def _richardson_derivative(f, x0, h):
 
 @pytest.mark.parametrize("center", [0, 1, 2, 3])
 @pytest.mark.parametrize("axis", [0, 1, 2])
-@pytest.mark.parametrize("lbase", [0, 1, 2])
+@pytest.mark.parametrize("lbase", [0, 1, 2, 3])
 def test_centre_derivative_raises_angular_momentum(center, axis, lbase):
     """x-power raising from a centre derivative, on every centre and axis.
 
@@ -219,7 +219,8 @@ def quadrature_eri(ls, al, R, u_lo=0.0, u_hi=None):
 
 @pytest.mark.parametrize("ls", [(1, 0, 0, 0), (1, 1, 0, 0), (0, 0, 1, 1), (1, 0, 1, 0),
                                 (2, 0, 1, 0), (2, 1, 0, 1), (2, 2, 0, 0), (2, 0, 2, 0),
-                                (3, 0, 1, 0), (1, 2, 2, 1), (3, 1, 2, 0), (2, 2, 2, 2)])
+                                (3, 0, 1, 0), (1, 2, 2, 1), (3, 1, 2, 0), (2, 2, 2, 2),
+                                (4, 0, 1, 0), (2, 1, 4, 0)])
 def test_eri_against_gaussian_transform_quadrature(ls):
     rng = np.random.default_rng(sum(l * 7 ** i for i, l in enumerate(ls)))
     al = np.exp(rng.uniform(np.log(0.2), np.log(3.0), size=4))

@@ -62,3 +62,22 @@ def test_padded_inputs_have_no_gradient():
     _, g = R.pinball_grad(theta, mu, isd, X, y, 0.7)
     W1g = g[R.OFF_W1:R.OFF_B1].reshape(16, 64)
     assert np.all(W1g[12:] == 0.0)
+
+
+def test_layer_inputs_are_bf16_rounded():
+    """A network that passes normalised feature 0 straight through (unit
+    weights, zero biases) returns that feature rounded to BF16 once (the
+    rounding is idempotent), and the unrounded value without rounding."""
+    th = np.zeros(R.NPARAM, np.float32)
+    th[R.OFF_W1 + 0 * R.NH + 0] = 1.0
+    th[R.OFF_W2 + 0 * R.NH + 0] = 1.0
+    th[R.OFF_W3 + 0] = 1.0
+    mu = np.zeros(16, np.float32)
+    isd = np.ones(16, np.float32)
+    x0 = np.array([1.0 + 2.0 ** -10, 3.0 + 2.0 ** -9, 0.75], np.float64)
+    X = np.zeros((3, 12), np.float32)
+    X[:, 0] = x0
+    y = R.forward(th, mu, isd, X)
+    assert np.array_equal(y, R.bf16_round(x0))
+    assert y[0] == 1.0 and y[1] == 3.0 and y[2] == 0.75
+    assert np.array_equal(R.forward(th, mu, isd, X, round_weights=False), X[:, 0].astype(np.float64))
