@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--tau32", type=float, default=1e-4)
     ap.add_argument("--graph", type=int, default=1, help="replay each build as one CUDA graph")
     ap.add_argument("--branches", type=int, default=4, help="class kernels forked over this many graph branches")
+    ap.add_argument("--micro", action="store_true", help="appendix-style micro-benchmarks instead of the workload")
     ap.add_argument("--tune", type=int, default=1, help="autotune the fragment shapes before the warm-up (untimed)")
     ap.add_argument("--prof-steps", type=int, default=1, help="serialised, per-kernel-timed steps after the timed region")
     return ap.parse_args()
@@ -483,10 +484,71 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_micro(args):
+    """Micro-benchmarks shaped like the paper's appendix (one JSON line):
+    (ss|ss) kernels with n_prim = 1..8 in FP64 and FP32 on a 96-atom cluster
+    geometry, and uncontracted d-only / f-only bases on a 192-atom cluster
+    geometry with n_dm = 1..4 (time split into a density-independent part and
+    a per-density part by a least-squares line in n_dm)."""
+    import numpy as np
+    import torch
+    from paper_2507_09772_gb300 import jk, synth
+
+    jk.load_library()
+
+    def geometry(nunits, seed):
+        rng = np.random.default_rng(seed)
+        xyz, _ = synth._triatomic_cluster(rng, nunits)
+        return xyz
+
+    def timed_build(eng, D, precision, reps=3):
+        eng.build(D, cutoff=args.cutoff, precision=precision, stats=True)   # compile, warm
+        ms, st = [], None
+        for _ in range(reps):
+            _, _, st = eng.build(D, cutoff=args.cutoff, precision=precision, stats=True)
+            ms.append(st["ms"])
+        return statistics.median(ms), st
+
+    rows = []
+    xyz = geometry(32, 2001)
+    for n in range(1, 9):
+        rng = np.random.default_rng(3000 + n)
+        exps = np.geomspace(30.0, 0.15, n) if n > 1 else np.array([0.8])
+        mol = synth.custom_basis_molecule(xyz, [[(0, exps)] for _ in range(len(xyz))], rng, name=f"s{n}")
+        eng = jk.JK(mol)
+        D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+        m64, s64 = timed_build(eng, D, "fp64")
+        m32, s32 = timed_build(eng, D, "fp32")
+        eng.close()
+        rows.append({"case": "(ss|ss)", "natm": len(xyz), "n_prim": n, "ms_fp64": m64, "ms_fp32": m32,
+                     "fp64_over_fp32": m64 / m32, "quartets": s64["quartets_fp64"],
+                     "prim_quartets": s64["prim_quartets"]})
+    xyz = geometry(64, 2002)
+    for l, name in ((2, "d-only"), (3, "f-only")):
+        rng = np.random.default_rng(4000 + l)
+        per_atom = [[(l, np.array([np.exp(rng.uniform(np.log(0.4), np.log(1.2)))]))] for _ in range(len(xyz))]
+        mol = synth.custom_basis_molecule(xyz, per_atom, rng, n_dm=4, name=name)
+        eng = jk.JK(mol)
+        pts = []
+        for ndm in range(1, 5):
+            D = torch.tensor(mol.D[:ndm], dtype=torch.float64, device="cuda")
+            ms, st = timed_build(eng, D, "fp64")
+            pts.append((ndm, ms))
+            rows.append({"case": name, "natm": len(xyz), "nao": mol.nao, "n_dm": ndm, "ms_fp64": ms,
+                         "quartets": st["quartets_fp64"]})
+        eng.close()
+        a = np.polyfit([p[0] for p in pts], [p[1] for p in pts], 1)
+        rows.append({"case": name, "fit": "ms = integrals + n_dm * per_density",
+                     "integrals_ms": float(a[1]), "per_density_ms": float(a[0])})
+    print(json.dumps({"micro": rows, "cutoff": args.cutoff, "data": "synthetic"}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.micro:
+        run_micro(args)
     else:
         run_ours(args)
 

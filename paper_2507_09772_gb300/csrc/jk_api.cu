@@ -59,12 +59,16 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
+// On failure the runtime's (non-sticky) last-error state is cleared, so that
+// it is not reported again by a later, unrelated check.
 #define CK(call)                                                                               \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
+        if (e_ != cudaSuccess) {                                                               \
+            (void)cudaGetLastError();                                                          \
             return fail(e_ == cudaErrorMemoryAllocation ? JK_ERR_OOM : JK_ERR_CUDA, "%s: %s",  \
                         #call, cudaGetErrorString(e_));                                        \
+        }                                                                                      \
     } while (0)
 
 // ------------------------------------------------------------ driver API
@@ -1366,7 +1370,10 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
 
     // Everything a build does on the device, in order, on stream s (and, for
     // nbranch > 1, forked onto the handle's side streams and joined back).
-    auto enqueue = [&](cudaStream_t s0) -> int {
+    // capturing: external event records become event nodes of the graph;
+    // outside a capture they are plain records
+    auto enqueue = [&](cudaStream_t s0, bool capturing) -> int {
+        const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         nlaunch_aux = 0;
         if (h->spherical) {
             dim3 g((unsigned)(((long long)max_nsh * max_nsh + 127) / 128), ndm, h->nmol);
@@ -1454,11 +1461,11 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             if (need < grid) grid = (int)std::max(1LL, need);
             void *params[] = {&a};
             // External records become event nodes when captured into a graph
-            if (prof) CK(cudaEventRecordWithFlags(h->prof_ev[2 * k], sk, cudaEventRecordExternal));
+            if (prof) CK(cudaEventRecordWithFlags(h->prof_ev[2 * k], sk, rec_flags));
             CUresult r = drv().launchKernel(ki[k].fn, grid, 1, 1, specs[k].block(), 1, 1, (unsigned)ki[k].smem,
                                             (CUstream)sk, params, nullptr);
             if (r != CUDA_SUCCESS) return fail(JK_ERR_CUDA, "launch of %s failed: %d", specs[k].name().c_str(), (int)r);
-            if (prof) CK(cudaEventRecordWithFlags(h->prof_ev[2 * k + 1], sk, cudaEventRecordExternal));
+            if (prof) CK(cudaEventRecordWithFlags(h->prof_ev[2 * k + 1], sk, rec_flags));
         }
         if (nbranch > 1) {
             for (int b = 1; b < nbranch; ++b) {
@@ -1498,7 +1505,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-            int erc = enqueue(h->cap);
+            int erc = enqueue(h->cap, true);
             cudaGraph_t graph = nullptr;
             cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
             if (erc) { if (graph) cudaGraphDestroy(graph); return erc; }
@@ -1512,7 +1519,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         nlaunch_aux = it->second.second;
         CK(cudaGraphLaunch(it->second.first, st));
     } else {
-        int erc = enqueue(st);
+        int erc = enqueue(st, false);
         if (erc) return erc;
     }
     if (stats) {

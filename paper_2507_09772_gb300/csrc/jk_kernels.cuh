@@ -45,6 +45,8 @@ __device__ constexpr int jk_cart_exp(int l, int idx, int axis)
 template <typename R> struct JkPP;
 template <> struct JkPP<double> { typedef JkPrimPair64 T; };
 template <> struct JkPP<float> { typedef JkPrimPair32 T; };
+__device__ __forceinline__ float jk_pp_q(const JkPrimPair64 &r) { return r.qf; }
+__device__ __forceinline__ float jk_pp_q(const JkPrimPair32 &r) { return r.q; }
 
 __device__ __forceinline__ double jk_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float jk_rsqrt(float x) { return rsqrtf(x); }
@@ -291,16 +293,20 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
     const PPT *bpp = pp + bra.pp_off;
     const PPT *kpp = pp + ket.pp_off;
     // primitive pairs are sorted by their Schwarz factor q (largest first):
-    // stop a loop at the first q_ij q_kl <= qthr (= prim_eps / Dmax)
-    const double qk0 = (double)kpp[0].q;
+    // stop a loop at the first q_ij q_kl <= qthr (= prim_eps / Dmax), compared
+    // in FP32 (a product below the FP32 range is below any threshold that
+    // matters; qthr < 0 screens nothing)
+    const float qthf = (float)qthr;
+    const float qk0 = jk_pp_q(kpp[0]);
     int nprim = 0;
 #pragma unroll 1
     for (int ij = 0; ij < NPA * NPB; ++ij) {
         const PPT bp = bpp[ij];
-        if ((double)bp.q * qk0 <= qthr) break;
+        const float qb = jk_pp_q(bp);
+        if (qb * qk0 <= qthf) break;
         for (int kl = 0; kl < NPC * NPD; ++kl) {
             const PPT kp = kpp[kl];
-            if ((double)bp.q * (double)kp.q <= qthr) break;
+            if (qb * jk_pp_q(kp) <= qthf) break;
             ++nprim;
             const R p = bp.p, q = kp.p;
             const R rpq = jk_rsqrt(p + q);

@@ -31,7 +31,9 @@ struct JkPair {
 struct JkPrimPair64 {
     double Px, Py, Pz, p;
     double PAx, PAy, PAz, K;
-    double inv2p, q, pad1, pad2;
+    double inv2p, q;
+    float qf, padf;   // qf: q rounded to FP32 (the primitive screen compares in FP32)
+    double pad2;
 };
 struct JkPrimPair32 {
     float Px, Py, Pz, p;

@@ -36,7 +36,8 @@ __global__ void jk_pairdata_kernel(int npair, const int *__restrict__ pa, const 
             r.K = ca * cb * exp(-al * be * ip * r2) * ip;
             r.inv2p = 0.5 * ip;
             r.q = 0.0;
-            r.pad1 = r.pad2 = 0.0;
+            r.qf = r.padf = 0.f;
+            r.pad2 = 0.0;
             out64[o] = r;
             JkPrimPair32 s;
             s.Px = (float)r.Px; s.Py = (float)r.Py; s.Pz = (float)r.Pz; s.p = (float)p;
@@ -248,6 +249,7 @@ __global__ void jk_primsort_kernel(int npair, const int *__restrict__ pp_off, co
         JkPrimPair64 r = in64[o + k];
         JkPrimPair32 s = in32[o + k];
         r.q = qk;
+        r.qf = (float)qk;
         s.q = (float)qk;
         out64[o + rank] = r;
         out32[o + rank] = s;
