@@ -234,7 +234,9 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets
                 "fp32_fraction": st["quartets_fp32"] / max(1, q), "quartets_routed": st["quartets_routed"],
                 "same_quartets_as_fp64": bool(q == fp64_quartets)}
 
-    tune = eng.autotune(Ds, cutoff=args.cutoff, precision="mixed") if args.tune else None
+    # the FP32 tier's shapes, tuned on all-FP32 builds (93% of the mixed quartets are FP32)
+    tune = (eng.autotune(Ds, cutoff=args.cutoff, precision="fp32", max_candidates=3, min_share=0.01)
+            if args.tune else None)
     out["mixed"] = timed("mixed")
     out["mixed"]["autotune"] = tune
     # router: labels from FP64 logging builds of held-out molecules shaped
@@ -307,7 +309,7 @@ def run_ours(args):
 
     tune = None
     if args.tune:
-        tune = eng.autotune(Ds, cutoff=args.cutoff, precision=args.precision)
+        tune = eng.autotune(Ds, cutoff=args.cutoff, precision=args.precision, max_candidates=3, min_share=0.01)
 
     def step(stats=True):
         flush.fill_(1)

@@ -746,6 +746,9 @@ struct jk_handle {
     std::vector<size_t> cart_off;          // per molecule offset into d_cart
     JkSphMol *d_sph = nullptr, *h_sph = nullptr;  // [0, nmol): to Cartesian, [nmol, 2 nmol): back
     size_t cart_gen = 0;                   // bumps when the scratch moves (invalidates graphs)
+    float *d_d32 = nullptr;                // FP32 copies of D for the FP32 tier: ndm x nao_c^2 per molecule
+    size_t d32_ndm = 0;
+    std::vector<size_t> d32_off;
     // learned router
     JkPairFeat *d_pfeat = nullptr;         // aligned with d_pairs
     JkRouterDev *d_router = nullptr;
@@ -776,7 +779,7 @@ void free_handle(jk_handle *h)
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     cudaFree(h->d_sh_l); cudaFree(h->d_sh_sph); cudaFree(h->d_sh_aou); cudaFree(h->d_c2s_off);
-    cudaFree(h->d_c2s); cudaFree(h->d_cart); cudaFree(h->d_sph);
+    cudaFree(h->d_c2s); cudaFree(h->d_cart); cudaFree(h->d_sph); cudaFree(h->d_d32);
     cudaFree(h->d_pfeat); cudaFree(h->d_router); cudaFree(h->d_logn);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -1313,6 +1316,19 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         h->cart_ndm = ndm;
         ++h->cart_gen;
     }
+    // FP32 copies of the densities when the FP32 tier runs
+    const bool use32 = mode != JK_PREC_FP64;
+    if (use32 && h->d32_ndm < (size_t)ndm) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(h->d_d32);
+        h->d_d32 = nullptr;
+        h->d32_off.assign(h->nmol, 0);
+        size_t tot = 0;
+        for (int m = 0; m < h->nmol; ++m) { h->d32_off[m] = tot; tot += (size_t)ndm * h->nao_cart[m] * h->nao_cart[m]; }
+        CK(cudaMalloc(&h->d_d32, sizeof(float) * std::max<size_t>(tot, 1)));
+        h->d32_ndm = ndm;
+        ++h->cart_gen;
+    }
     // per-molecule descriptors
     CK(cudaEventSynchronize(h->mol_copied));
     long long off = 0;
@@ -1343,6 +1359,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                 b = JkSphMol{};
             }
         }
+        x.D32 = use32 ? h->d_d32 + h->d32_off[m] : nullptr;
         x.nsh = h->mol_sh0[m + 1] - h->mol_sh0[m];
         x.dmax_off = off;
         off += (long long)x.nsh * x.nsh;
@@ -1396,6 +1413,13 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                                                   h->d_dmax, h->d_dmax_mol, h->d_err);
         CK(cudaGetLastError());
         ++nlaunch_aux;
+        if (use32) {
+            long long per = (long long)ndm * max_nao * max_nao;
+            dim3 g((unsigned)std::min<long long>((per + 255) / 256, 4096), h->nmol);
+            jk_d32_kernel<<<g, 256, 0, s0>>>(h->d_mols, ndm);
+            CK(cudaGetLastError());
+            ++nlaunch_aux;
+        }
         if (nbranch > 1) {
             CK(cudaEventRecord(h->ev_fork, s0));
             for (int b = 1; b < nbranch; ++b) CK(cudaStreamWaitEvent(h->side[b - 1], h->ev_fork, 0));

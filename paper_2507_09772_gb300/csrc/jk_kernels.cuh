@@ -496,6 +496,10 @@ __device__ __forceinline__ void jk_log_sample(const JkClassArgs &args, const JkP
 // ------------------------------------------ contraction with the density
 // The thread's fragment T of (ab|cd), degeneracy f: J_ab partial kept in
 // jab (flushed once per bra pair), the other five blocks by FP64 atomics.
+template <typename R> __device__ __forceinline__ const R *jk_dens(const JkMol &mol);
+template <> __device__ __forceinline__ const double *jk_dens<double>(const JkMol &mol) { return mol.D; }
+template <> __device__ __forceinline__ const float *jk_dens<float>(const JkMol &mol) { return mol.D32; }
+
 template <int FA, int FB, int FC, int FD, int NDM, int DOJ, int DOK, typename R>
 __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f, const JkMol &mol,
                                             int a0, int b0, int c0, int d0, R (&jab)[NDM][FA][FB])
@@ -504,7 +508,8 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
     const int nao = mol.nao;
 #pragma unroll
     for (int m = 0; m < NDM; ++m) {
-        const double *D = mol.D + m * nn;
+        // the tier's own copy of D (the FP32 tier reads a pre-rounded one)
+        const R *D = jk_dens<R>(mol) + m * nn;
         if (DOJ) {
             R Dcd[FC][FD], Dab[FA][FB];
 #pragma unroll

@@ -78,10 +78,11 @@ __device__ __forceinline__ void jk_router_features(const JkPairFeat &fa, const J
     x[6] = __fsqrt_rn(r2);
     x[7] = fa.lq;
     x[8] = fc.lq;
-    // log10 in double, rounded once to float: identical in every kernel
-    x[9] = (float)log10(dmax > 1e-300 ? dmax : 1e-300);
+    // FP32 logarithms (the FP64 ones cost dozens of FP64-pipe instructions
+    // per lane); the same code in every kernel gives the same bits
+    x[9] = log10f(fmaxf((float)dmax, 1e-30f));
     x[10] = __fadd_rn(fa.lsum, fc.lsum);
-    x[11] = (float)log10(B / tau);
+    x[11] = log10f(__fdiv_rn((float)B, (float)tau));
 }
 
 // Prediction (margin included) for the candidate this lane holds; every lane

@@ -44,6 +44,7 @@ struct JkPrimPair32 {
 // Per molecule of a handle.
 struct JkMol {
     const double *D;   // n_dm x nao x nao (Cartesian)
+    const float *D32;  // the same rounded to FP32, read by the FP32 tier (nullptr when it does not run)
     double *J;         // half-matrix accumulator X, symmetrised after the build
     double *K;         // half-matrix accumulator Y
     int nao;           // Cartesian functions

@@ -155,6 +155,17 @@ __global__ void jk_zero_kernel(const JkMol *__restrict__ mols, int ndm)
     }
 }
 
+// FP32 copy of every molecule's densities for the FP32 tier (one rounding
+// per element, as the tier would apply on every load).
+__global__ void jk_d32_kernel(const JkMol *__restrict__ mols, int ndm)
+{
+    const JkMol mol = mols[blockIdx.y];
+    float *dst = const_cast<float *>(mol.D32);
+    const long long n = (long long)ndm * mol.nao * mol.nao;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)mol.D[i];
+}
+
 // Spherical <-> Cartesian transforms, one thread per (shell a, shell b)
 // block of one molecule and density. c2s holds, per l, the ncart(l) x (2l+1)
 // coefficients (row-major) at c2s_off[l]; a Cartesian shell uses the
