@@ -708,6 +708,7 @@ struct jk_handle {
     JkPrimPair32 *d_pp32 = nullptr;
     JkMol *d_mols = nullptr;
     double *d_dmax = nullptr;
+    float *d_dmax32 = nullptr;
     unsigned long long *d_dmax_mol = nullptr;
     double *d_rys64 = nullptr;
     float *d_rys32 = nullptr;
@@ -771,7 +772,7 @@ void free_handle(jk_handle *h)
     for (auto &L : h->launches) cudaFree(L.d_prefix);
     cudaFree(h->d_sh_mol); cudaFree(h->d_mol_sh0); cudaFree(h->d_sh_ao); cudaFree(h->d_sh_nc);
     cudaFree(h->d_pairs); cudaFree(h->d_pp64); cudaFree(h->d_pp32); cudaFree(h->d_mols);
-    cudaFree(h->d_dmax); cudaFree(h->d_dmax_mol); cudaFree(h->d_rys64); cudaFree(h->d_rys32);
+    cudaFree(h->d_dmax); cudaFree(h->d_dmax32); cudaFree(h->d_dmax_mol); cudaFree(h->d_rys64); cudaFree(h->d_rys32);
     cudaFree(h->d_work); cudaFree(h->d_stats); cudaFree(h->d_err); cudaFree(h->d_tile_off);
     if (h->h_mols) cudaFreeHost(h->h_mols);
     if (h->mol_copied) cudaEventDestroy(h->mol_copied);
@@ -953,7 +954,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
         const double *A = coords + 3 * shells[a].atom, *B = coords + 3 * shells[b].atom;
         p.Ax = A[0]; p.Ay = A[1]; p.Az = A[2];
         p.ABx = A[0] - B[0]; p.ABy = A[1] - B[1]; p.ABz = A[2] - B[2];
-        p.Q = 0; p.pad = 0;
+        p.Q = 0; p.Qf = 0.f; p.padf = 0.f;
     }
     JkPair *d_cp = nullptr;
     double *d_q = nullptr;
@@ -1086,7 +1087,11 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
         return q[x] > q[y];
     });
     h->h_pairs.resize(order.size());
-    for (size_t k = 0; k < order.size(); ++k) { h->h_pairs[k] = cp[order[k]]; h->h_pairs[k].Q = q[order[k]]; }
+    for (size_t k = 0; k < order.size(); ++k) {
+        h->h_pairs[k] = cp[order[k]];
+        h->h_pairs[k].Q = q[order[k]];
+        h->h_pairs[k].Qf = (float)q[order[k]];
+    }
     size_t k0 = 0;
     while (k0 < order.size()) {
         size_t k1 = k0;
@@ -1210,6 +1215,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     h->ntiles = toff[nmol];
     if ((rc = upload(&h->d_tile_off, toff))) return rc;
     CK(cudaMalloc(&h->d_dmax, sizeof(double) * dtot));
+    CK(cudaMalloc(&h->d_dmax32, sizeof(float) * dtot));
     CK(cudaMalloc(&h->d_dmax_mol, sizeof(unsigned long long) * nmol));
     CK(cudaMalloc(&h->d_mols, sizeof(JkMol) * nmol));
     const size_t nl = h->launches.size() * 2;
@@ -1410,7 +1416,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 3 * nl, s0));
         CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, s0));
         jk_dmax_kernel<<<h->nshell, 128, 0, s0>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
-                                                  h->d_dmax, h->d_dmax_mol, h->d_err);
+                                                  h->d_dmax, h->d_dmax32, h->d_dmax_mol, h->d_err);
         CK(cudaGetLastError());
         ++nlaunch_aux;
         if (use32) {
@@ -1438,6 +1444,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.pp32 = h->d_pp32;
             a.mols = h->d_mols;
             a.dmax = h->d_dmax;
+            a.dmax32 = h->d_dmax32;
             a.dmax_mol = reinterpret_cast<const double *>(h->d_dmax_mol);
             a.rys64 = h->d_rys64;
             a.rys32 = h->d_rys32;
@@ -1461,6 +1468,12 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.router = h->d_router;
             a.tau = tau;
             a.band_hi = band_hi;
+            // FP32 screening unless the lower bound is below the FP32 range
+            a.scr32 = a.lo >= 1e-30 ? 1 : 0;
+            a.lo32 = (float)a.lo;
+            a.hi32 = std::isinf(a.hi) ? INFINITY : (float)a.hi;
+            a.tau32 = (float)tau;
+            a.band_hi32 = (float)band_hi;
             a.tier = tier[k];
             a.log_x = logs ? logs->x : nullptr;
             a.log_y = logs ? logs->y : nullptr;
@@ -1473,6 +1486,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.item_hi = nunits * (h->part_index + 1) / h->part_count;
             a.chunk = JK_CHUNK;
             a.prim_eps = std::min(cutoff, h->prim_eps);
+            a.prim_eps32 = (float)a.prim_eps;
             a.omega = std::fabs(h->omega);
             a.same_class = (L.c1 == L.c2) ? 1 : 0;
             a.with_j = with_j ? 1 : 0;

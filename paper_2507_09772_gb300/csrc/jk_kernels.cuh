@@ -278,7 +278,7 @@ __device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, in
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
           int GA, int GB, int GC, int GD, typename R, int OP = 0,
           int NT = JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>::G>
-__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, double qthr, double omega,
+__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, float qthr, double omega,
                                            const typename JkPP<R>::T *__restrict__ pp,
                                            const R *__restrict__ rys, R *grp, unsigned gmask, int tg, bool act,
                                            const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>> &off,
@@ -296,7 +296,7 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
     // stop a loop at the first q_ij q_kl <= qthr (= prim_eps / Dmax), compared
     // in FP32 (a product below the FP32 range is below any threshold that
     // matters; qthr < 0 screens nothing)
-    const float qthf = (float)qthr;
+    const float qthf = qthr;
     const float qk0 = jk_pp_q(kpp[0]);
     int nprim = 0;
 #pragma unroll 1
@@ -410,27 +410,27 @@ template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassA
 template <int MODE>
 __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
                                                 const double *dmx, double dmol, int j, int ke, bool &sig,
-                                                bool &stop, bool &band, double &dmq, double &Bout);
+                                                bool &stop, bool &band, float &dmq, float &Bout);
 // Keep (bra, ket j) iff lo < Q_ab Q_cd Dmax <= hi; `stop` when even the
 // molecule's largest density element cannot lift this ket (and every later
 // one, kets being sorted by Q) above lo.
 template <int MODE>
 __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkPairFeat &braf,
                                           const JkMol &mol, const double *dmx, double dmol, int j, int ke,
-                                          bool &sig, bool &stop, bool &band, double &dmq, unsigned short *rsm)
+                                          bool &sig, bool &stop, bool &band, float &dmq, unsigned short *rsm)
 {
     sig = false;
     stop = false;
     band = false;
-    dmq = 1.0;
-    double B = 0.0;
+    dmq = 1.0f;
+    float B = 0.0f;
     jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, j, ke, sig, stop, band, dmq, B);
     if (MODE == 1) {
         // learned router for the band candidates, all lanes together on the tensor cores
         if (__ballot_sync(0xffffffffu, band)) {
             const JkPairFeat kf = band ? args.ket_feat[j] : braf;
-            const bool to32 = jk_router_to_fp32_warp(args.router, braf, kf, band ? B : 2.0 * args.tau,
-                                                     band ? dmq : 1.0, args.tau, rsm);
+            const bool to32 = jk_router_to_fp32_warp(args.router, braf, kf, band ? B : 2.0f * args.tau32,
+                                                     band ? dmq : 1.0f, args.tau32, rsm);
             if (band) sig = (args.tier == 1) ? to32 : !to32;
         }
         band = band && sig;
@@ -440,14 +440,39 @@ __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair 
 template <int MODE>
 __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
                                                 const double *dmx, double dmol, int j, int ke, bool &sig,
-                                                bool &stop, bool &band, double &dmq, double &Bout)
+                                                bool &stop, bool &band, float &dmq, float &Bout)
 {
     if (j >= ke) return;
-    const double bq = bra.Q * args.ket[j].Q;
+    const JkPair &kt = args.ket[j];
+    if (args.scr32) {
+        // FP32 path: a handful of FP32 operations per candidate instead of
+        // FP64-pipe work (the FP32 tier's whole budget on GB300)
+        const float bq = bra.Qf * __ldg(&kt.Qf);
+        if (bq * (float)dmol <= args.lo32) { stop = true; return; }
+        float dm = 1.0f;
+        if (args.use_dmax) {
+            const float *d32 = args.dmax32 + mol.dmax_off;
+            const int c = __ldg(&kt.a_loc), d = __ldg(&kt.b_loc);
+            const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
+            dm = 0.0f;
+            if (args.with_j) dm = fmaxf(__ldg(d32 + a * ns + b), __ldg(d32 + c * ns + d));
+            if (args.with_k) {
+                dm = fmaxf(dm, fmaxf(__ldg(d32 + a * ns + c), __ldg(d32 + a * ns + d)));
+                dm = fmaxf(dm, fmaxf(__ldg(d32 + b * ns + c), __ldg(d32 + b * ns + d)));
+            }
+        }
+        dmq = dm;
+        const float B = bq * dm;
+        Bout = B;
+        sig = (B > args.lo32) && (B <= args.hi32);
+        band = MODE == 1 && sig && B > args.tau32 && B <= args.band_hi32;
+        return;
+    }
+    const double bq = bra.Q * kt.Q;
     if (bq * dmol <= args.lo) { stop = true; return; }
     double dm = 1.0;
     if (args.use_dmax) {
-        const int c = args.ket[j].a_loc, d = args.ket[j].b_loc;
+        const int c = kt.a_loc, d = kt.b_loc;
         const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
         dm = 0.0;
         if (args.with_j) dm = fmax(__ldg(dmx + a * ns + b), __ldg(dmx + c * ns + d));
@@ -456,9 +481,11 @@ __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const J
             dm = fmax(dm, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
         }
     }
-    dmq = dm;
+    // dm below the FP32 range only reaches here with lo < 1e-30, where the
+    // primitive threshold is 0 and dmq only divides it
+    dmq = (float)dm;
     const double B = bq * dm;
-    Bout = B;
+    Bout = (float)B;
     sig = (B > args.lo) && (B <= args.hi);
     band = MODE == 1 && sig && B > args.tau && B <= args.band_hi;
 }
@@ -488,7 +515,8 @@ __device__ __forceinline__ void jk_log_sample(const JkClassArgs &args, const JkP
     const unsigned long long idx = atomicAdd(args.log_n, 1ull);
     if ((long long)idx >= args.log_cap) return;
     float x[JK_RT_NIN];
-    jk_router_features(braf, ketf, B, dm, args.tau, x);
+    // the bound as the FP32 screening path forms it
+    jk_router_features(braf, ketf, (bra.Qf * ket.Qf) * (float)dm, (float)dm, args.tau32, x);
     for (int i = 0; i < JK_RT_NIN; ++i) args.log_x[idx * JK_RT_NIN + i] = x[i];
     args.log_y[idx] = (float)log10(fmax(tmax, 1e-300) / (bra.Q * ket.Q));
 }
@@ -705,7 +733,7 @@ jk_class_kernel(const JkClassArgs args)
             unsigned long long nq = 0, nband = 0, nprim = 0;
             for (int base = kb; base < ke; base += 32) {
                 bool sig, stop, band;
-                double dmq;
+                float dmq;
                 jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, rsm);
                 unsigned mask = __ballot_sync(0xffffffffu, sig);
                 nq += __popc(mask);
@@ -719,14 +747,15 @@ jk_class_kernel(const JkClassArgs args)
                     }
 #pragma unroll 1
                     for (int q = 0; q < NGW && mask; ++q) mask &= mask - 1;
-                    const double dmk = __shfl_sync(0xffffffffu, dmq, myket >= 0 ? myket - base : 0);
+                    const float dmk = __shfl_sync(0xffffffffu, dmq, myket >= 0 ? myket - base : 0);
                     if (myket >= 0) {
                         const JkPair ket = args.ket[myket];
                         R T[S::EPT];
 #pragma unroll
                         for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
                         const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP>(
-                            bra, ket, args.prim_eps / dmk, args.omega, pp, rys, grp, gmask, tg, true, off, T);
+                            bra, ket, __fdiv_rn(args.prim_eps32, dmk), args.omega, pp, rys, grp, gmask, tg, true,
+                            off, T);
                         if (tg == 0) nprim += np;
                         R f = (R)1;
                         if (bra.a == bra.b) f *= (R)0.5;
@@ -760,7 +789,7 @@ jk_class_kernel(const JkClassArgs args)
         // one group (or one of its X slabs) per CTA of round_up(G / X, 32) threads
         constexpr int NTC = G / X;
         __shared__ long long s_item;
-        __shared__ double s_dm[32];
+        __shared__ float s_dm[32];
         __shared__ unsigned s_mask;
         __shared__ int s_stop;
         __shared__ __align__(16) unsigned short s_rsm[MODE == 1 ? 32 * JK_RT_NINP : 2];
@@ -810,7 +839,7 @@ jk_class_kernel(const JkClassArgs args)
             for (int base = kb; base < ke; base += 32) {
                 if (threadIdx.x < 32) {
                     bool sig, stop, band;
-                    double dmq;
+                    float dmq;
                     jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, s_rsm);
                     s_dm[lane] = dmq;
                     const unsigned msk = __ballot_sync(0xffffffffu, sig);
@@ -831,7 +860,8 @@ jk_class_kernel(const JkClassArgs args)
 #pragma unroll
                     for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
                     const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP, NTC>(
-                        bra, ket, args.prim_eps / s_dm[myket - base], args.omega, pp, rys, grp, 0u, tg, act, off, T);
+                        bra, ket, __fdiv_rn(args.prim_eps32, s_dm[myket - base]), args.omega, pp, rys, grp, 0u, tg,
+                        act, off, T);
                     nprim += np;
                     if (act) {
                         R f = (R)1;
@@ -914,7 +944,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
                 double T[S::EPT];
 #pragma unroll
                 for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0, 0.0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
+                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0f, 0.0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
                 if (ga == gc && gb == gd) {
 #pragma unroll
                     for (int ia = 0; ia < FA; ++ia)
@@ -950,7 +980,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
 #pragma unroll
             for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
             jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double, 0, NTC>(
-                pr, pr, -1.0, 0.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
+                pr, pr, -1.0f, 0.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
             double mx = 0.0;
             if (act && ga == gc && gb == gd) {
 #pragma unroll

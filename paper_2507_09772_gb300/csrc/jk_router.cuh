@@ -64,8 +64,8 @@ __device__ __forceinline__ void jk_mma_bf16(float (&d)[4], const unsigned (&a)[4
 }
 
 // Features of quartet (ab|cd) with bound B and density factor dmax.
-__device__ __forceinline__ void jk_router_features(const JkPairFeat &fa, const JkPairFeat &fc, double B,
-                                                   double dmax, double tau, float x[JK_RT_NIN])
+__device__ __forceinline__ void jk_router_features(const JkPairFeat &fa, const JkPairFeat &fc, float B,
+                                                   float dmax, float tau, float x[JK_RT_NIN])
 {
     const float dx = __fadd_rn(fa.pcx, -fc.pcx), dy = __fadd_rn(fa.pcy, -fc.pcy), dz = __fadd_rn(fa.pcz, -fc.pcz);
     const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
@@ -80,9 +80,9 @@ __device__ __forceinline__ void jk_router_features(const JkPairFeat &fa, const J
     x[8] = fc.lq;
     // FP32 logarithms (the FP64 ones cost dozens of FP64-pipe instructions
     // per lane); the same code in every kernel gives the same bits
-    x[9] = log10f(fmaxf((float)dmax, 1e-30f));
+    x[9] = log10f(fmaxf(dmax, 1e-30f));
     x[10] = __fadd_rn(fa.lsum, fc.lsum);
-    x[11] = log10f(__fdiv_rn((float)B, (float)tau));
+    x[11] = log10f(__fdiv_rn(B, tau));
 }
 
 // Prediction (margin included) for the candidate this lane holds; every lane
@@ -165,7 +165,7 @@ __device__ __forceinline__ float jk_router_warp(const JkRouterDev *__restrict__ 
 
 // FP32 route decisions for the band candidates of a warp (warp-synchronous).
 __device__ __forceinline__ bool jk_router_to_fp32_warp(const JkRouterDev *__restrict__ R, const JkPairFeat &fa,
-                                                       const JkPairFeat &fc, double B, double dmax, double tau,
+                                                       const JkPairFeat &fc, float B, float dmax, float tau,
                                                        unsigned short *sm)
 {
     float x[JK_RT_NIN];

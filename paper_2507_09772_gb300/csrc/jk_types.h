@@ -16,7 +16,8 @@ struct JkPair {
     double Q;          // Schwarz factor sqrt(max |(mu nu|mu nu)|)
     double Ax, Ay, Az; // centre of shell a
     double ABx, ABy, ABz;  // A - B (horizontal recurrence)
-    double pad;
+    float Qf;              // Q rounded to FP32 (the FP32 screening path)
+    float padf;
 };
 
 // Per primitive pair (alpha_i on a, beta_j on b), p = alpha + beta:
@@ -65,6 +66,7 @@ struct JkClassArgs {
     const JkPrimPair32 *pp32;
     const JkMol *mols;
     const double *dmax;          // block max |D| tables, all molecules
+    const float *dmax32;         // the same rounded to FP32
     const double *dmax_mol;      // per molecule: max over its table
     const double *rys64;         // FP64 Rys tables
     const float *rys32;          // FP32 Rys tables
@@ -77,6 +79,11 @@ struct JkClassArgs {
     unsigned long long *stats;   // [0] quartets, [1] primitive quartets, [2] routed band quartets
     int *err;                    // device error word
     double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi
+    // FP32 screening (scr32 = 1, used when lo >= 1e-30 so that no product of
+    // interest leaves the FP32 range): the same bounds and the band in FP32;
+    // every tier of a build evaluates them identically
+    int scr32;
+    float lo32, hi32, tau32, band_hi32, prim_eps32;
     int nbra;
     int same_class;              // ket class == bra class: ket index >= bra index
     int with_j, with_k;          // which outputs (and density blocks) to use

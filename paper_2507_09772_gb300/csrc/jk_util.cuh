@@ -54,7 +54,8 @@ __global__ void jk_pairdata_kernel(int npair, const int *__restrict__ pa, const 
 __global__ void jk_dmax_kernel(const JkMol *__restrict__ mols, const int *__restrict__ sh_mol,
                                const int *__restrict__ mol_sh0, const int *__restrict__ sh_ao,
                                const int *__restrict__ sh_nc, int ndm, double *__restrict__ dmax,
-                               unsigned long long *__restrict__ dmax_mol, int *__restrict__ err)
+                               float *__restrict__ dmax32, unsigned long long *__restrict__ dmax_mol,
+                               int *__restrict__ err)
 {
     const int s = blockIdx.x;
     const int m = sh_mol[s];
@@ -77,6 +78,7 @@ __global__ void jk_dmax_kernel(const JkMol *__restrict__ mols, const int *__rest
                 }
         if (bad) atomicOr(err, JK_ERR_DEV_NAN);
         dmax[mol.dmax_off + (long long)a * mol.nsh + b] = mx;
+        dmax32[mol.dmax_off + (long long)a * mol.nsh + b] = (float)mx;
         rowmax = fmax(rowmax, mx);
     }
     for (int o = 16; o > 0; o >>= 1) rowmax = fmax(rowmax, __shfl_xor_sync(0xffffffffu, rowmax, o));
