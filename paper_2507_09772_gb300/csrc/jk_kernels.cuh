@@ -700,6 +700,9 @@ jk_class_kernel(const JkClassArgs args)
         R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
         // router scratch, 1 KB per warp (MODE 1)
         __shared__ __align__(16) unsigned short s_rsm[MODE == 1 ? 4 * 32 * JK_RT_NINP : 2];
+        // ket queue per warp: at most NGW - 1 + 32 entries
+        __shared__ int s_qk[4][64];
+        __shared__ float s_qd[4][64];
         unsigned short *rsm = s_rsm + (MODE == 1 ? wib * 32 * JK_RT_NINP : 0);
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
@@ -731,23 +734,33 @@ jk_class_kernel(const JkClassArgs args)
 #pragma unroll
                     for (int j = 0; j < FB; ++j) jab[m][i][j] = (R)0;
             unsigned long long nq = 0, nband = 0, nprim = 0;
+            // significant kets wait in a per-warp queue (in scan order) until
+            // a round can give every group of the warp one; partial rounds
+            // only at the end of the item
+            int qn = 0;
             for (int base = kb; base < ke; base += 32) {
                 bool sig, stop, band;
                 float dmq;
                 jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, rsm);
-                unsigned mask = __ballot_sync(0xffffffffu, sig);
+                const unsigned mask = __ballot_sync(0xffffffffu, sig);
                 nq += __popc(mask);
                 if (MODE == 1) nband += __popc(__ballot_sync(0xffffffffu, band));
-                while (mask) {
+                if (sig) {
+                    const int pos = qn + __popc(mask & ((1u << lane) - 1u));
+                    s_qk[wib][pos] = base + lane;
+                    s_qd[wib][pos] = dmq;
+                }
+                qn += __popc(mask);
+                __syncwarp();
+                const bool last = __any_sync(0xffffffffu, stop) || base + 32 >= ke;
+                while (qn >= NGW || (last && qn > 0)) {
+                    const int take = qn < NGW ? qn : NGW;
                     int myket = -1;
-                    if (active) {
-                        unsigned mm = mask;
-                        for (int q = 0; q < gw && mm; ++q) mm &= mm - 1;
-                        if (mm) myket = base + __ffs(mm) - 1;
+                    float dmk = 1.0f;
+                    if (active && gw < take) {
+                        myket = s_qk[wib][gw];
+                        dmk = s_qd[wib][gw];
                     }
-#pragma unroll 1
-                    for (int q = 0; q < NGW && mask; ++q) mask &= mask - 1;
-                    const float dmk = __shfl_sync(0xffffffffu, dmq, myket >= 0 ? myket - base : 0);
                     if (myket >= 0) {
                         const JkPair ket = args.ket[myket];
                         R T[S::EPT];
@@ -773,9 +786,18 @@ jk_class_kernel(const JkClassArgs args)
                                               jk_quartet_dmax(args, bra, ket, mol, dmx), tm);
                         }
                     }
+                    // drop the round's entries (at most 31 remain)
                     __syncwarp();
+                    const int rest = qn - take;
+                    int k2 = 0;
+                    float d2 = 0.0f;
+                    if (lane < rest) { k2 = s_qk[wib][take + lane]; d2 = s_qd[wib][take + lane]; }
+                    __syncwarp();
+                    if (lane < rest) { s_qk[wib][lane] = k2; s_qd[wib][lane] = d2; }
+                    __syncwarp();
+                    qn = rest;
                 }
-                if (__any_sync(0xffffffffu, stop)) break;
+                if (last) break;
             }
             if (DOJ && active) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
             for (int o = 16; o > 0; o >>= 1) nprim += __shfl_xor_sync(0xffffffffu, nprim, o);
