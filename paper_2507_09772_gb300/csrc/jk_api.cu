@@ -104,6 +104,10 @@ Driver &drv()
     return d;
 }
 
+static_assert(sizeof(JkPair) == 96 && sizeof(JkPrimPair64) == 96 && sizeof(JkPrimPair32) == 48 &&
+                  sizeof(JkPairFeat) == 32,
+              "record sizes are part of the device layout");
+
 // ------------------------------------------------------------ kernel spec
 int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 

@@ -34,7 +34,7 @@ struct JkRouterDev {
 };
 
 // Per shell pair, for the features (host-computed at init).
-struct JkPairFeat {
+struct alignas(16) JkPairFeat {
     float lpmin, lpmax;   // ln of the smallest / largest primitive exponent sum
     float rab;            // |A - B| (bohr)
     float lq;             // log10 Q_ab

@@ -7,7 +7,8 @@
 // (l, then nprim) is >= that of b. Pairs of one pair class are stored
 // contiguously, grouped by molecule and sorted by descending Q inside a
 // molecule, so that a ket scan can stop at the first Q that fails the bound.
-struct JkPair {
+// 16-byte alignment: records that lanes gather load as 16-byte vectors
+struct alignas(16) JkPair {
     int a, b;          // global shell indices
     int mol;           // molecule index
     int pp_off;        // first primitive pair (na*nb of them, a-major)
@@ -29,14 +30,14 @@ struct JkPair {
 //          included); a shell pair's primitive pairs are sorted by q,
 //          largest first, so primitive loops can stop at the first
 //          q_ij q_kl Dmax at or below the primitive threshold
-struct JkPrimPair64 {
+struct alignas(16) JkPrimPair64 {
     double Px, Py, Pz, p;
     double PAx, PAy, PAz, K;
     double inv2p, q;
     float qf, padf;   // qf: q rounded to FP32 (the primitive screen compares in FP32)
     double pad2;
 };
-struct JkPrimPair32 {
+struct alignas(16) JkPrimPair32 {
     float Px, Py, Pz, p;
     float PAx, PAy, PAz, K;
     float inv2p, q, pad1, pad2;
