@@ -40,6 +40,31 @@ WORKLOAD = "batched-631gs-64mol"
 PEAK_FP64_NOMINAL = 152 * 4 * 2.07e9
 PEAK_FP32_NOMINAL = 152 * 256 * 2.07e9
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the largest class kernels, from one ncu capture of the 8-molecule case
+# (`bench.py --nmol 8 ... --tune 0`, heuristic fragment shapes), scaled to
+# the 64-molecule launch by its quartet count. Valid only for the kernel
+# sources they were taken with (hash below) and the same threads per
+# quartet; otherwise the roofline reports traffic null.
+TRAFFIC_SOURCES = ["paper_2507_09772_gb300/csrc/jk_kernels.cuh", "paper_2507_09772_gb300/csrc/jk_types.h",
+                   "paper_2507_09772_gb300/csrc/jk_router.cuh", "paper_2507_09772_gb300/csrc/jk_api.cu"]
+TRAFFIC_SHA = "d5369a7d5ce253e1"
+TRAFFIC_BYTES = {   # (kernel label, threads per quartet): bytes per full-size launch
+    ("jk_class_kernel<(21|10) prims 1113, fp64>", 2): 13381376 * 20995695 / 2141233,
+    ("jk_class_kernel<(11|11) prims 3111, fp64>", 3): 3046400 * 12299763 / 1246899,
+}
+
+
+def traffic_for(label, g):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != TRAFFIC_SHA:
+        return None
+    return TRAFFIC_BYTES.get((label, g))
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -376,12 +401,16 @@ def run_ours(args):
     peak = PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL
     probe = (jk.jk_measure_peak("fp64" if dom["tier"] == 0 else "fp32", 100.0) if not args.no_probe
              else (PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL))
+    dom_label = "jk_class_kernel<(%d%d|%d%d) prims %d%d%d%d, %s>" % (
+        dom["la"], dom["lb"], dom["lc"], dom["ld"], dom["na"], dom["nb"], dom["nc"], dom["nd"],
+        "fp64" if dom["tier"] == 0 else "fp32")
+    traffic = traffic_for(dom_label, dom["threads_per_quartet"])
     roofline = {
         "bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-        "frac": dom_flops / (dom_ms * 1e-3) / peak, "traffic": None,
-        "kernel": "jk_class_kernel<(%d%d|%d%d) prims %d%d%d%d, %s>" % (
-            dom["la"], dom["lb"], dom["lc"], dom["ld"], dom["na"], dom["nb"], dom["nc"], dom["nd"],
-            "fp64" if dom["tier"] == 0 else "fp32"),
+        "frac": dom_flops / (dom_ms * 1e-3) / peak, "traffic": traffic,
+        "traffic_note": ("DRAM bytes per launch from an 8-molecule ncu capture scaled by quartets; "
+                         "%.2f GB/s over the launch" % (traffic / (dom_ms * 1e-3) / 1e9)) if traffic else None,
+        "kernel": dom_label,
         "kernel_share": dom["ms"] / ms_serial,
         "launch_ms": dom_ms, "launches": dom["launches"],
         "timing": "CUDA events around each launch, serialised replay after the timed region",
