@@ -700,9 +700,12 @@ jk_class_kernel(const JkClassArgs args)
         R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
         // router scratch, 1 KB per warp (MODE 1)
         __shared__ __align__(16) unsigned short s_rsm[MODE == 1 ? 4 * 32 * JK_RT_NINP : 2];
-        // ket queue per warp: at most NGW - 1 + 32 entries
+        // ket queue per warp: at most NGW - 1 + 32 entries; band queue (MODE 1):
+        // at most 31 + 32
         __shared__ int s_qk[4][64];
         __shared__ float s_qd[4][64];
+        __shared__ int s_bk[4][MODE == 1 ? 64 : 1];
+        __shared__ float s_bd[4][MODE == 1 ? 64 : 1], s_bb[4][MODE == 1 ? 64 : 1];
         unsigned short *rsm = s_rsm + (MODE == 1 ? wib * 32 * JK_RT_NINP : 0);
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
@@ -737,23 +740,71 @@ jk_class_kernel(const JkClassArgs args)
             // significant kets wait in a per-warp queue (in scan order) until
             // a round can give every group of the warp one; partial rounds
             // only at the end of the item
-            int qn = 0;
+            // MODE 1: band candidates wait in a second queue and go through
+            // the router 32 at a time (one full MMA tile per evaluation);
+            // those this tier keeps join the ket queue
+            int qn = 0, nb = 0;
             for (int base = kb; base < ke; base += 32) {
-                bool sig, stop, band;
-                float dmq;
-                jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, rsm);
-                const unsigned mask = __ballot_sync(0xffffffffu, sig);
-                nq += __popc(mask);
-                if (MODE == 1) nband += __popc(__ballot_sync(0xffffffffu, band));
-                if (sig) {
-                    const int pos = qn + __popc(mask & ((1u << lane) - 1u));
+                bool sig = false, stop = false, band = false;
+                float dmq = 1.0f, B = 0.0f;
+                jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, B);
+                const unsigned lt = (1u << lane) - 1u;
+                const bool def = sig && !band;   // decided by the bounds alone
+                const unsigned mdef = __ballot_sync(0xffffffffu, def);
+                nq += __popc(mdef);
+                if (def) {
+                    const int pos = qn + __popc(mdef & lt);
                     s_qk[wib][pos] = base + lane;
                     s_qd[wib][pos] = dmq;
                 }
-                qn += __popc(mask);
+                qn += __popc(mdef);
+                if (MODE == 1) {
+                    const unsigned mb = __ballot_sync(0xffffffffu, band);
+                    if (band) {
+                        const int pos = nb + __popc(mb & lt);
+                        s_bk[wib][pos] = base + lane;
+                        s_bd[wib][pos] = dmq;
+                        s_bb[wib][pos] = B;
+                    }
+                    nb += __popc(mb);
+                }
                 __syncwarp();
                 const bool last = __any_sync(0xffffffffu, stop) || base + 32 >= ke;
-                while (qn >= NGW || (last && qn > 0)) {
+                for (;;) {
+                    const bool full_round = qn >= NGW;
+                    const bool band_batch = MODE == 1 && !full_round && (nb >= 32 || (last && nb > 0));
+                    const bool tail_round = !full_round && !band_batch && last && qn > 0;
+                    if (band_batch) {
+                        const int take = nb < 32 ? nb : 32;
+                        const bool mine = lane < take;
+                        const int j = mine ? s_bk[wib][lane] : 0;
+                        const float dj = mine ? s_bd[wib][lane] : 1.0f;
+                        const float bj = mine ? s_bb[wib][lane] : 2.0f * args.tau32;
+                        const JkPairFeat kf = mine ? args.ket_feat[j] : braf;
+                        const bool to32 = jk_router_to_fp32_warp(args.router, braf, kf, bj, dj, args.tau32, rsm);
+                        const bool keep = mine && ((args.tier == 1) ? to32 : !to32);
+                        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                        nq += __popc(mk);
+                        nband += __popc(mk);
+                        if (keep) {
+                            const int pos = qn + __popc(mk & lt);
+                            s_qk[wib][pos] = j;
+                            s_qd[wib][pos] = dj;
+                        }
+                        qn += __popc(mk);
+                        // drop the evaluated band entries (at most 31 remain)
+                        __syncwarp();
+                        const int rest = nb - take;
+                        int k2 = 0;
+                        float d2 = 0.0f, b2 = 0.0f;
+                        if (lane < rest) { k2 = s_bk[wib][take + lane]; d2 = s_bd[wib][take + lane]; b2 = s_bb[wib][take + lane]; }
+                        __syncwarp();
+                        if (lane < rest) { s_bk[wib][lane] = k2; s_bd[wib][lane] = d2; s_bb[wib][lane] = b2; }
+                        __syncwarp();
+                        nb = rest;
+                        continue;
+                    }
+                    if (!full_round && !tail_round) break;
                     const int take = qn < NGW ? qn : NGW;
                     int myket = -1;
                     float dmk = 1.0f;
