@@ -101,56 +101,72 @@ __device__ __forceinline__ float jk_router_warp(const JkRouterDev *__restrict__ 
     }
     __syncwarp();
     const unsigned *smw = reinterpret_cast<const unsigned *>(sm);
-    float out[2][4];
+    const uint2 *W1 = reinterpret_cast<const uint2 *>(R->W1p);
+    const uint2 *W2 = reinterpret_cast<const uint2 *>(R->W2p);
+    const uint2 *W3 = reinterpret_cast<const uint2 *>(R->W3p);
+    // Each weight fragment is loaded once and applied to both 16-row tiles
+    // at once; layer 2 is computed 16 output columns at a time and folded
+    // straight into layer 3, so only the first hidden layer stays live.
+    unsigned h1[2][4][4];
+    {
+        unsigned a[2][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = mt * 16 + g, r1 = r0 + 8;
-        unsigned a[4];
-        a[0] = smw[(r0 * JK_RT_NINP + 2 * t) >> 1];
-        a[1] = smw[(r1 * JK_RT_NINP + 2 * t) >> 1];
-        a[2] = smw[(r0 * JK_RT_NINP + 2 * t + 8) >> 1];
-        a[3] = smw[(r1 * JK_RT_NINP + 2 * t + 8) >> 1];
-        // layer 1: 16 -> 64, bias in the accumulator, ReLU, BF16 -> A of layer 2
-        unsigned h1[4][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float c[4];
-            c[0] = c[2] = __ldg(&R->b1[nt * 8 + 2 * t]);
-            c[1] = c[3] = __ldg(&R->b1[nt * 8 + 2 * t + 1]);
-            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R->W1p) + nt * 32 + lane);
-            jk_mma_bf16(c, a, b.x, b.y);
-            const int ks = nt >> 1, half = nt & 1;
-            h1[ks][half * 2 + 0] = jk_pack_bf16(fmaxf(c[0], 0.0f), fmaxf(c[1], 0.0f));
-            h1[ks][half * 2 + 1] = jk_pack_bf16(fmaxf(c[2], 0.0f), fmaxf(c[3], 0.0f));
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = mt * 16 + g, r1 = r0 + 8;
+            a[mt][0] = smw[(r0 * JK_RT_NINP + 2 * t) >> 1];
+            a[mt][1] = smw[(r1 * JK_RT_NINP + 2 * t) >> 1];
+            a[mt][2] = smw[(r0 * JK_RT_NINP + 2 * t + 8) >> 1];
+            a[mt][3] = smw[(r1 * JK_RT_NINP + 2 * t + 8) >> 1];
         }
-        // A fragments of layer 2 for k-step ks: {rows g: cols 2t..} = h1[ks][0],
-        // {g+8} = h1[ks][1], {g, +8 cols} = h1[ks][2], {g+8, +8} = h1[ks][3]
-        unsigned h2[4][4];
+        // layer 1: 16 -> 64, bias in the accumulator, ReLU, BF16 -> A of layer 2
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
-            float c[4];
-            c[0] = c[2] = __ldg(&R->b2[nt * 8 + 2 * t]);
-            c[1] = c[3] = __ldg(&R->b2[nt * 8 + 2 * t + 1]);
+            const uint2 b = __ldg(W1 + nt * 32 + lane);
+            const float bl = __ldg(&R->b1[nt * 8 + 2 * t]), bh = __ldg(&R->b1[nt * 8 + 2 * t + 1]);
+            const int ks = nt >> 1, half = nt & 1;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                float c[4] = {bl, bh, bl, bh};
+                jk_mma_bf16(c, a[mt], b.x, b.y);
+                // A fragments of layer 2 for k-step ks: {rows g: cols 2t..} = h1[ks][0],
+                // {g+8} = h1[ks][1], {g, +8 cols} = h1[ks][2], {g+8, +8} = h1[ks][3]
+                h1[mt][ks][half * 2 + 0] = jk_pack_bf16(fmaxf(c[0], 0.0f), fmaxf(c[1], 0.0f));
+                h1[mt][ks][half * 2 + 1] = jk_pack_bf16(fmaxf(c[2], 0.0f), fmaxf(c[3], 0.0f));
+            }
+        }
+    }
+    // layers 2 and 3: layer-3 k-step k3 takes layer-2 n-tiles 2 k3 and 2 k3 + 1
+    float o[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int k3 = 0; k3 < 4; ++k3) {
+        unsigned a3[2][4];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int nt = 2 * k3 + half;
+            const float bl = __ldg(&R->b2[nt * 8 + 2 * t]), bh = __ldg(&R->b2[nt * 8 + 2 * t + 1]);
+            float c[2][4] = {{bl, bh, bl, bh}, {bl, bh, bl, bh}};
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-                const unsigned a2[4] = {h1[ks][0], h1[ks][1], h1[ks][2], h1[ks][3]};
-                const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R->W2p) + (ks * 8 + nt) * 32 + lane);
-                jk_mma_bf16(c, a2, b.x, b.y);
+                const uint2 b = __ldg(W2 + (ks * 8 + nt) * 32 + lane);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) jk_mma_bf16(c[mt], h1[mt][ks], b.x, b.y);
             }
-            const int ks = nt >> 1, half = nt & 1;
-            h2[ks][half * 2 + 0] = jk_pack_bf16(fmaxf(c[0], 0.0f), fmaxf(c[1], 0.0f));
-            h2[ks][half * 2 + 1] = jk_pack_bf16(fmaxf(c[2], 0.0f), fmaxf(c[3], 0.0f));
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                a3[mt][half * 2 + 0] = jk_pack_bf16(fmaxf(c[mt][0], 0.0f), fmaxf(c[mt][1], 0.0f));
+                a3[mt][half * 2 + 1] = jk_pack_bf16(fmaxf(c[mt][2], 0.0f), fmaxf(c[mt][3], 0.0f));
+            }
         }
         // layer 3: 64 -> 1 (an 8-wide n-tile, column 0 used)
-        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const uint2 b = __ldg(W3 + k3 * 32 + lane);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            const unsigned a3[4] = {h2[ks][0], h2[ks][1], h2[ks][2], h2[ks][3]};
-            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R->W3p) + ks * 32 + lane);
-            jk_mma_bf16(c, a3, b.x, b.y);
-        }
-        out[mt][0] = c[0];
-        out[mt][1] = c[2];
+        for (int mt = 0; mt < 2; ++mt) jk_mma_bf16(o[mt], a3[mt], b.x, b.y);
+    }
+    float out[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        out[mt][0] = o[mt][0];
+        out[mt][1] = o[mt][2];
     }
     __syncwarp();
     // row r of tile mt sits in lane 4 (r % 8), register c0 (r < 8) or c2
