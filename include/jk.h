@@ -148,7 +148,9 @@ int jk_init_batch(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *sh
 
 /* J and K for a single-molecule handle (see the conventions above).
  * cutoff: quartets with Q_ab Q_cd Dmax <= cutoff are skipped (the paper uses
- * 1e-13). precision_mode: JK_PREC_*. stats may be NULL. */
+ * 1e-13); for cutoff >= 1e-30 the bound and the tier thresholds are compared
+ * in FP32 (every tier alike, so each quartet runs exactly once), below it in
+ * FP64. precision_mode: JK_PREC_*. stats may be NULL. */
 int jk_build(jk_handle *h, const double *D, int32_t n_dm, int with_j, int with_k, double cutoff,
              int precision_mode, double *J, double *K, void *stream, jk_stats *stats);
 
