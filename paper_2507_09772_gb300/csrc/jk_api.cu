@@ -1472,8 +1472,10 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.router = h->d_router;
             a.tau = tau;
             a.band_hi = band_hi;
-            // FP32 screening unless the lower bound is below the FP32 range
-            a.scr32 = a.lo >= 1e-30 ? 1 : 0;
+            // FP32 screening unless the cutoff is below the FP32 range; one
+            // choice for every launch of the build, so that the tiers of a
+            // mixed build compare the same bounds in the same precision
+            a.scr32 = cutoff >= 1e-30 ? 1 : 0;
             a.lo32 = (float)a.lo;
             a.hi32 = std::isinf(a.hi) ? INFINITY : (float)a.hi;
             a.tau32 = (float)tau;

@@ -80,9 +80,9 @@ struct JkClassArgs {
     unsigned long long *stats;   // [0] quartets, [1] primitive quartets, [2] routed band quartets
     int *err;                    // device error word
     double lo, hi;               // keep a quartet iff lo < Q_ab Q_cd Dmax <= hi
-    // FP32 screening (scr32 = 1, used when lo >= 1e-30 so that no product of
-    // interest leaves the FP32 range): the same bounds and the band in FP32;
-    // every tier of a build evaluates them identically
+    // FP32 screening (scr32 = 1, used when the build's cutoff is >= 1e-30 so
+    // that no product of interest leaves the FP32 range): the same bounds and
+    // the band in FP32; every tier of a build evaluates them identically
     int scr32;
     float lo32, hi32, tau32, band_hi32, prim_eps32;
     int nbra;

@@ -447,3 +447,15 @@ def test_g_shells_mixed_precision():
     Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
     check(mol, J, Jr, TOL_MIXED, "J")
     check(mol, K, Kr, TOL_MIXED, "K")
+
+
+def test_mixed_precision_at_cutoff_zero_runs_every_quartet_once():
+    """With cutoff 0 every tier screens in FP64 (one precision per build), so
+    the tiers still partition the quartets exactly."""
+    mol = synth.tiny_631gs()
+    _, _, s64 = gpu_jk(mol, cutoff=0.0, precision="fp64")
+    J, K, sm = gpu_jk(mol, cutoff=0.0, precision="mixed")
+    assert sm["quartets_fp64"] + sm["quartets_fp32"] == s64["quartets_fp64"]
+    Jr, Kr, _ = oracle.jk(mol, cutoff=0.0)
+    check(mol, J, Jr, TOL_MIXED, "J")
+    check(mol, K, Kr, TOL_MIXED, "K")
