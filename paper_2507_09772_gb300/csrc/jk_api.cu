@@ -450,10 +450,14 @@ std::vector<double> solid_harmonics(int l)
 
 // -------------------------------------------------------- fragment choice
 // Threads per quartet: G = ga*gb*gc*gd with each g dividing the Cartesian
-// size of its shell and G <= 32. G == 1 keeps the 2D tables in registers and
-// is taken when elements plus tables stay small; otherwise the smallest G
-// whose per-thread fragment fits the register budget (the 1qnt grid search
-// of Sec. 3.2 refines this per device through the tuning table).
+// size of its shell. G == 1 keeps the 2D tables in registers and is taken
+// when elements plus tables stay small; otherwise the smallest G whose
+// per-thread fragment fits the register budget within one CTA (G <= 32: a
+// warp holds 32 / G groups; up to 256, or 1024 for the Schwarz kernels: one
+// group per CTA), else the smallest G that fits when the group is split
+// over gx CTAs of at most 256 threads. The autotuner (the 1qnt grid search
+// of Sec. 3.2, run on the caller's data) refines the choice per device
+// through the tuning table.
 void choose_fragments(KSpec &s, bool symmetric)
 {
     const int nf[4] = {ncart(s.la), ncart(s.lb), ncart(s.lc), ncart(s.ld)};
