@@ -353,16 +353,19 @@ def run_ours(args):
     sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0.record(stream)
     stats = []
-    for _ in range(args.steps):
+    for i in range(args.steps):
         stats.append(step())
+        step_ev[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     clocks = sampler.stop()
     ms_total = e0.elapsed_time(e1)
+    step_ms = [(e0 if i == 0 else step_ev[i - 1]).elapsed_time(step_ev[i]) for i in range(args.steps)]
 
     # Per-kernel launch durations: CUDA events around every class kernel, on
     # the stream it runs on, in steps replayed with the kernels serialised
@@ -490,6 +493,8 @@ def run_ours(args):
             "path_fp64_roofline": path_fp64,
             "autotune": tune,
             "serial_ms_per_step": ms_serial / args.prof_steps,
+            "step_ms": ({"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}
+                        if step_ms else None),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "forms": forms,
