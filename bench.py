@@ -223,6 +223,28 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def tier_split(eng, Ds, Js, Ks, args, precision):
+    """Class-kernel time per tier of one serialised, per-launch-timed build
+    (CUDA events around each launch, one graph branch)."""
+    from paper_2507_09772_gb300 import jk
+    try:
+        eng.set_option("profile", 1)
+        eng.set_option("branches", 1)
+        eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)
+        ms = {0: 0.0, 1: 0.0}
+        q = {0: 0, 1: 0}
+        for p in jk.jk_profile(eng.h):
+            ms[p["tier"]] += p["ms"]
+            q[p["tier"]] += p["quartets"]
+        return {"fp64_kernels_ms": ms[0], "fp32_kernels_ms": ms[1], "fp64_quartets": q[0], "fp32_quartets": q[1],
+                "timing": "serialised replay, CUDA events around each class launch"}
+    except Exception as e:   # a diagnostic, never the reason a run fails
+        return {"error": str(e)[:200]}
+    finally:
+        eng.set_option("profile", 0)
+        eng.set_option("branches", args.branches)
+
+
 def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets):
     """Mixed (Schwarz x Dmax tiering) and routed (learned router in the band)
     builds of the same batch, timed like the FP64 steps, with their largest
@@ -264,6 +286,7 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets
             if args.tune else None)
     out["mixed"] = timed("mixed")
     out["mixed"]["autotune"] = tune
+    out["mixed"]["tiers"] = tier_split(eng, Ds, Js, Ks, args, "mixed")
     # router: labels from FP64 logging builds of held-out molecules shaped
     # like the batched and cluster workloads (not the ones timed here),
     # trained on the GPU, then routed builds of the workload
@@ -284,6 +307,7 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets
     train_s = time.perf_counter() - t0
     eng.load_router(blob)
     r = timed("routed")
+    r["tiers"] = tier_split(eng, Ds, Js, Ks, args, "routed")
     r.update({"train_samples": int(n), "train_s": train_s, "train_loss_first": tst["loss_first"],
               "train_loss_last": tst["loss_last"],
               "train_set": "FP64 labels of 6 held-out batch molecules and a 64-unit cluster"})
