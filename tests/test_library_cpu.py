@@ -120,3 +120,15 @@ def test_fragment_candidates_reject_bad_arguments(lib):
         jk.jk_fragment_candidates(5, 0, 0, 0)
     with pytest.raises(jk.JKError):
         jk.jk_fragment_candidates(1, 1, 1, 1, max_candidates=0)
+
+
+def test_group_split_over_ctas_compiles(lib, tmp_path, monkeypatch):
+    """(gg|gg) needs more than 256 threads within the fragment budget: its
+    quartets are split over several CTAs (threads per quartet above 256);
+    the class kernel and the Schwarz kernels of a g basis compile for sm_103a."""
+    monkeypatch.setenv("JK_KERNEL_CACHE", str(tmp_path))
+    g, _ = jk.jk_compile_class(4, 4, 4, 4, 1, 1, 1, 1)
+    assert g > 256
+    shells = np.array([[0, 4, 1, 0, 0, 0]], dtype=np.int32)
+    nk, _ = jk.jk_compile_basis(shells)
+    assert nk == 1 * 2 + 1
