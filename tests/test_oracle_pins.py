@@ -488,3 +488,25 @@ def test_range_separated_jk_is_symmetric_and_ordered():
     # both attenuated operators are positive definite
     for J in (Jl, Js):
         assert np.einsum("ij,ij->", D, J[0]) > 0
+
+
+def test_g_shell_molecule_screened_equals_brute_force_and_einsum():
+    """With g shells (l = 4): the symmetric screened builder equals the
+    brute-force builder over every shell quartet and the einsum of the full
+    ERI tensor, and J, K stay symmetric with tr(DJ), tr(DK) >= 0."""
+    rng = np.random.default_rng(404)
+    xyz = np.array([[0.0, 0.0, 0.0], [1.2, 0.4, -0.3]])
+    per_atom = [[(0, [2.5, 0.4]), (4, [0.9])], [(1, [0.7]), (4, [1.3])]]
+    mol = synth.custom_basis_molecule(xyz, per_atom, rng, name="g-pin")
+    J1, K1, _ = oracle.jk(mol, cutoff=0.0, method="brute")
+    J2, K2, _ = oracle.jk(mol, cutoff=0.0, method="screened")
+    assert np.abs(J1 - J2).max() < 1e-12 * max(1.0, np.abs(J1).max())
+    assert np.abs(K1 - K2).max() < 1e-12 * max(1.0, np.abs(K1).max())
+    eri = oracle.eri_full(mol)
+    D = mol.D[0]
+    Je = np.einsum("ijkl,kl->ij", eri, D)
+    Ke = np.einsum("ijkl,jl->ik", eri, D)
+    assert np.abs(J2[0] - Je).max() < 1e-12 * max(1.0, np.abs(Je).max())
+    assert np.abs(K2[0] - Ke).max() < 1e-12 * max(1.0, np.abs(Ke).max())
+    assert np.abs(J2[0] - J2[0].T).max() < 1e-13 and np.abs(K2[0] - K2[0].T).max() < 1e-13
+    assert np.trace(D @ J2[0]) >= 0 and np.trace(D @ K2[0]) >= 0
