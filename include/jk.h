@@ -194,6 +194,9 @@ int jk_info(jk_handle *h, int32_t mol, int32_t *nao, int32_t *nshell, int32_t *n
  * (zero for pairs dropped at init). */
 int jk_schwarz(jk_handle *h, double *Q_host);
 
+/* Synchronises the device, then frees everything the handle owns (device
+ * tables and scratch, captured graphs, streams, events); the caller's D, J
+ * and K are untouched. JK_ERR_ARG for NULL. */
 int jk_destroy(jk_handle *h);
 
 /* Router training data from a full FP64 build (which it also returns in J,
