@@ -184,6 +184,11 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * descriptor copied before each launch, so changing buffers is allowed.
  * JK_ERR_ARG for an unknown key. */
 int jk_set_option(jk_handle *h, const char *key, double value);
+/* Reads any option above, and the read-only figures "graphs" (captured
+ * graphs held), "init_ms" (jk_init wall time), "compile_ms" (NVRTC time spent
+ * by this handle), "npairs", "nclasses", "nlaunches" (significant shell
+ * pairs, pair classes, class-pair launches per tier). JK_ERR_ARG for an
+ * unknown key. */
 int jk_get_option(jk_handle *h, const char *key, double *value);
 
 /* Number of molecules, basis functions of molecule m (in the basis D is
