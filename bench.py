@@ -549,7 +549,10 @@ def run_micro(args):
     (ss|ss) kernels with n_prim = 1..8 in FP64 and FP32 on a 96-atom cluster
     geometry, and uncontracted d-only / f-only bases on a 192-atom cluster
     geometry with n_dm = 1..4 (time split into a density-independent part and
-    a per-density part by a least-squares line in n_dm)."""
+    a per-density part by a least-squares line in n_dm); then the extended
+    forms on 8 molecules of the batched workload (erf / erfc range
+    separation, J only, K only, an incremental build of a 1e-8 change) and a
+    12-atom uncontracted s p d f g basis (FP64 and mixed)."""
     import numpy as np
     import torch
     from paper_2507_09772_gb300 import jk, synth
@@ -600,6 +603,58 @@ def run_micro(args):
         a = np.polyfit([p[0] for p in pts], [p[1] for p in pts], 1)
         rows.append({"case": name, "fit": "ms = integrals + n_dm * per_density",
                      "integrals_ms": float(a[1]), "per_density_ms": float(a[0])})
+    # the "next" forms on 8 molecules of the batched workload: range
+    # separation, J-only / K-only, and an incremental build of a small change
+    mols = synth.batched_631gs(8)
+    eng = jk.JK(mols)
+    Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
+    for name, opts, kw in (("coulomb", {}, {}), ("erf w=0.3", {"omega": 0.3}, {}),
+                           ("erfc w=0.3", {"omega": -0.3}, {}), ("J only", {}, {"with_k": False}),
+                           ("K only", {}, {"with_j": False})):
+        try:
+            for k, v in opts.items():
+                eng.set_option(k, v)
+            eng.build(Ds, cutoff=args.cutoff, stats=True, **kw)
+            ms = []
+            for _ in range(3):
+                _, _, st = eng.build(Ds, cutoff=args.cutoff, stats=True, **kw)
+                ms.append(st["ms"])
+            rows.append({"case": "batch8 " + name, "ms_fp64": statistics.median(ms),
+                         "quartets": st["quartets_fp64"]})
+        except Exception as e:
+            rows.append({"case": "batch8 " + name, "error": str(e)[:200]})
+        finally:
+            eng.set_option("omega", 0.0)
+    try:
+        rng = np.random.default_rng(9)
+        dD = [torch.tensor(1e-8 * (lambda x: x + x.T)(rng.standard_normal(m.D.shape[1:]))[None],
+                           dtype=torch.float64, device="cuda") for m in mols]
+        eng.build(dD, cutoff=args.cutoff, stats=True)
+        ms = []
+        for _ in range(3):
+            _, _, st = eng.build(dD, cutoff=args.cutoff, stats=True)
+            ms.append(st["ms"])
+        rows.append({"case": "batch8 incremental |dD| ~ 1e-8", "ms_fp64": statistics.median(ms),
+                     "quartets": st["quartets_fp64"]})
+    except Exception as e:
+        rows.append({"case": "batch8 incremental", "error": str(e)[:200]})
+    eng.close()
+    # g shells: 12 atoms, uncontracted s p d f g on each
+    try:
+        rng = np.random.default_rng(4004)
+        xyz = geometry(4, 2003)
+        per_atom = [[(l, np.array([np.exp(rng.uniform(np.log(0.3), np.log(2.0)))])) for l in range(5)]
+                    for _ in range(len(xyz))]
+        mol = synth.custom_basis_molecule(xyz, per_atom, rng, name="spdfg")
+        eng = jk.JK(mol)
+        D = torch.tensor(mol.D, dtype=torch.float64, device="cuda")
+        m64, s64 = timed_build(eng, D, "fp64")
+        m32, _ = timed_build(eng, D, "mixed")
+        eng.close()
+        rows.append({"case": "spdfg uncontracted", "natm": len(xyz), "nao": mol.nao, "ms_fp64": m64,
+                     "ms_mixed": m32, "quartets": s64["quartets_fp64"]})
+    except Exception as e:
+        rows.append({"case": "spdfg uncontracted", "error": str(e)[:200]})
     print(json.dumps({"micro": rows, "cutoff": args.cutoff, "data": "synthetic"}))
 
 
