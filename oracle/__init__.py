@@ -200,7 +200,10 @@ _current_omega = [0.0]
 
 
 def dmax(mol, Dcart) -> np.ndarray:
-    """Shell-block max |D| over all densities (Cartesian D)."""
+    """Shell-block max |D| over all densities (Cartesian D): the density
+    factor of the screening bound of Sec. 2. Pinned against a numpy block
+    maximum over two densities, and through the kept quartet counts and the
+    restricted-einsum J, K of the screening rule."""
     sh = np.ascontiguousarray(mol.shells, dtype=np.int32)
     nsh = sh.shape[0]
     Dc = np.ascontiguousarray(Dcart, dtype=np.float64)

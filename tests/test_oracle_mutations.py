@@ -38,6 +38,11 @@ MUTATIONS = {
                                "Yk[I * nao + L] += v * Dk[Jx * nao + L];"),
     "J_ket_update_factor": ("Xk[Kx * nao + L] += 2.0 * v * Dk[I * nao + Jx];",
                             "Xk[Kx * nao + L] += v * Dk[I * nao + Jx];"),
+    "dmax_row_offset_dropped": ("double v = fabs(D[((size_t)k * nao + off[a] + i) * nao + off[b] + j]);",
+                                "double v = fabs(D[((size_t)k * nao + off[a]) * nao + off[b] + j]);"),
+    "dmax_first_density_only": ("            for (int k = 0; k < ndm; ++k)\n                for (int i = 0; i < ncart(sh[a].l); ++i)",
+                                "            for (int k = 0; k < 1; ++k)\n                for (int i = 0; i < ncart(sh[a].l); ++i)"),
+    "bound_drops_K_block_bd": ("            dm = fmax(dm, Dm[b * nsh + d]);\n", ""),
     "schwarz_wrong_diagonal": ("double v = fabs(blk[((i * nb + j) * na + i) * nb + j]);",
                                "double v = fabs(blk[((i * nb + i) * na + j) * nb + j]);"),
 }

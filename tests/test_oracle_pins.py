@@ -510,3 +510,174 @@ def test_g_shell_molecule_screened_equals_brute_force_and_einsum():
     assert np.abs(K2[0] - Ke).max() < 1e-12 * max(1.0, np.abs(Ke).max())
     assert np.abs(J2[0] - J2[0].T).max() < 1e-13 and np.abs(K2[0] - K2[0].T).max() < 1e-13
     assert np.trace(D @ J2[0]) >= 0 and np.trace(D @ K2[0]) >= 0
+
+
+# ------------------------------------------- density maxima and screening
+# The screening rule of Sec. 2 (eq:schwartz times the density bound): a shell
+# quartet (ab|cd) is kept iff Q_ab Q_cd Dmax > cutoff, with Dmax the largest
+# |D| over every density in the blocks the requested outputs read (ab, cd for
+# J; ac, ad, bc, bd for K). These pins restate the block maximum and the rule
+# in numpy, independently of the C code, and check (1) the block maxima
+# exactly, (2) the kept counts exactly, (3) J and K equal to the einsum of the
+# full ERI tensor restricted to the kept quartets, and (4) the error against
+# the unscreened einsum within the Schwarz bound of the dropped quartets.
+def _shell_offsets(mol):
+    return np.cumsum([0] + [oracle.ncart(int(l)) for l in mol.shells[:, 1]])
+
+
+def _np_block_max(mol, Dcart):
+    off = _shell_offsets(mol)
+    A = np.abs(Dcart).max(axis=0)
+    n = mol.nshell
+    out = np.zeros((n, n))
+    for a in range(n):
+        for b in range(n):
+            out[a, b] = A[off[a]:off[a + 1], off[b]:off[b + 1]].max()
+    return out
+
+
+def _np_schwarz_from_tensor(mol, eri):
+    off = _shell_offsets(mol)
+    diag = np.abs(np.einsum("ijij->ij", eri))
+    n = mol.nshell
+    Q = np.zeros((n, n))
+    for a in range(n):
+        for b in range(n):
+            Q[a, b] = math.sqrt(diag[off[a]:off[a + 1], off[b]:off[b + 1]].max())
+    return Q
+
+
+def _np_kept(Q, Dm, cutoff, with_j, with_k):
+    """Kept mask over every ordered shell quartet (a, b, c, d)."""
+    n = Q.shape[0]
+    dm = np.zeros((n, n, n, n))
+    if with_j:
+        dm = np.maximum(dm, Dm[:, :, None, None])
+        dm = np.maximum(dm, Dm[None, None, :, :])
+    if with_k:
+        dm = np.maximum(dm, Dm[:, None, :, None])   # ac
+        dm = np.maximum(dm, Dm[:, None, None, :])   # ad
+        dm = np.maximum(dm, Dm[None, :, :, None])   # bc
+        dm = np.maximum(dm, Dm[None, :, None, :])   # bd
+    # the same product order as the rule states it: (Q_ab Q_cd) Dmax
+    B = (Q[:, :, None, None] * Q[None, None, :, :]) * dm
+    return B > cutoff
+
+
+def _n_unique(mask):
+    n = mask.shape[0]
+    cnt = 0
+    for a in range(n):
+        for b in range(a + 1):
+            for c in range(n):
+                for d in range(c + 1):
+                    if a * (a + 1) // 2 + b >= c * (c + 1) // 2 + d and mask[a, b, c, d]:
+                        cnt += 1
+    return cnt
+
+
+def _g_screen_molecule():
+    """Two atoms 3 Å apart with s, p and g shells (tight and diffuse), so
+    that the rule drops a good share of the quartets at 1e-8 and 1e-4."""
+    rng = np.random.default_rng(404)
+    xyz = np.array([[0.0, 0.0, 0.0], [3.0, 0.4, -0.3]])
+    per_atom = [[(0, [2.5, 0.4]), (4, [0.9]), (0, [8.0])], [(1, [0.7]), (4, [1.3]), (0, [6.0])]]
+    return synth.custom_basis_molecule(xyz, per_atom, rng, name="g-screen")
+
+
+def _two_densities(mol, seed):
+    """D1 the molecule's own density; D2 a symmetric random matrix whose
+    elements are scaled so that each density holds the largest element of
+    some shell blocks."""
+    rng = np.random.default_rng(seed)
+    D1 = mol.D[0]
+    R = rng.standard_normal(D1.shape) * np.exp(rng.uniform(-3.0, 1.0, size=D1.shape))
+    D2 = 0.5 * np.abs(D1).max() * (R + R.T) / np.abs(R + R.T).max()
+    return np.stack([D1, D2])
+
+
+def test_density_block_max_matches_numpy_over_two_densities(tiny):
+    Dboth = _two_densities(tiny, 11)
+    got = oracle.dmax(tiny, Dboth)
+    ref = _np_block_max(tiny, Dboth)
+    assert np.array_equal(got, ref)
+    # both densities decide some blocks, and blocks of every l pair occur
+    m1 = _np_block_max(tiny, Dboth[:1])
+    m2 = _np_block_max(tiny, Dboth[1:])
+    assert (m1 > m2).any() and (m2 > m1).any()
+    assert len({(int(tiny.shells[a, 1]), int(tiny.shells[b, 1]))
+                for a in range(tiny.nshell) for b in range(tiny.nshell)}) == 9
+
+
+@pytest.fixture(scope="module")
+def screening_cases(tiny, tiny_eri):
+    g = _g_screen_molecule()
+    return [("tiny", tiny, tiny_eri, _two_densities(tiny, 12)),
+            ("g-screen", g, oracle.eri_full(g), _two_densities(g, 13))]
+
+
+@pytest.mark.parametrize("cutoff", [1e-8, 1e-4])
+@pytest.mark.parametrize("with_j,with_k", [(1, 1), (1, 0), (0, 1)])
+def test_screening_rule_kept_set_and_result(screening_cases, cutoff, with_j, with_k):
+    for name, mol, eri, D in screening_cases:
+        Q = _np_schwarz_from_tensor(mol, eri)
+        Dm = _np_block_max(mol, D)
+        mask = _np_kept(Q, Dm, cutoff, with_j, with_k)
+        assert 0 < mask.sum() < mask.size, name   # the rule drops something and keeps something
+        J1, K1, n1 = oracle.jk(mol, D=D, cutoff=cutoff, with_j=with_j, with_k=with_k, method="brute", Q=Q)
+        J2, K2, n2 = oracle.jk(mol, D=D, cutoff=cutoff, with_j=with_j, with_k=with_k, method="screened", Q=Q)
+        assert n1 == int(mask.sum()), name
+        assert n2 == _n_unique(mask), name
+        off = _shell_offsets(mol)
+        sh_of = np.repeat(np.arange(mol.nshell), np.diff(off))
+        M = mask[np.ix_(sh_of, sh_of, sh_of, sh_of)]
+        kept = eri * M
+        scale = max(1.0, np.abs(eri).max() * np.abs(D).max() * mol.nao ** 2)
+        for m in range(D.shape[0]):
+            if with_j:
+                Jm = np.einsum("ijkl,kl->ij", kept, D[m])
+                assert np.abs(J1[m] - Jm).max() < 1e-13 * scale, name
+                assert np.abs(J2[m] - Jm).max() < 1e-13 * scale, name
+            if with_k:
+                Km = np.einsum("ijkl,jl->ik", kept, D[m])
+                assert np.abs(K1[m] - Km).max() < 1e-13 * scale, name
+                assert np.abs(K2[m] - Km).max() < 1e-13 * scale, name
+
+
+@pytest.mark.parametrize("cutoff", [1e-8, 1e-4])
+@pytest.mark.parametrize("with_j,with_k", [(1, 1), (1, 0), (0, 1)])
+def test_screening_error_within_schwarz_bound_of_dropped_quartets(screening_cases, cutoff, with_j, with_k):
+    """|J - J_full| and |K - K_full| (J_full, K_full: einsum of the whole ERI
+    tensor) are at most the sum, over the quartets the rule drops, of
+    Q_ab Q_cd max|D in the contracted block| times the block size (eq:schwartz
+    bounds every element of a block by Q_ab Q_cd)."""
+    for name, mol, eri, D in screening_cases:
+        Q = _np_schwarz_from_tensor(mol, eri)
+        Dm = _np_block_max(mol, D)
+        drop = ~_np_kept(Q, Dm, cutoff, with_j, with_k)
+        assert drop.any(), name
+        off = _shell_offsets(mol)
+        nf = np.diff(off).astype(float)
+        sh_of = np.repeat(np.arange(mol.nshell), nf.astype(int))
+        J, K, _ = oracle.jk(mol, D=D, cutoff=cutoff, with_j=with_j, with_k=with_k, method="screened", Q=Q)
+        QQ = Q[:, :, None, None] * Q[None, None, :, :] * drop
+        # J_ab element: sum over dropped (c, d) of Q_ab Q_cd max|D_cd| N_c N_d
+        jb = np.einsum("abcd,cd->ab", QQ, Dm * np.outer(nf, nf))
+        # K_ac element: sum over dropped (b, d) of Q_ab Q_cd max|D_bd| N_b N_d
+        kb = np.einsum("abcd,bd->ac", QQ, Dm * np.outer(nf, nf))
+        Jb = jb[np.ix_(sh_of, sh_of)]
+        Kb = kb[np.ix_(sh_of, sh_of)]
+        for m in range(D.shape[0]):
+            if with_j:
+                Jf = np.einsum("ijkl,kl->ij", eri, D[m])
+                err = np.abs(J[m] - Jf)
+                # plus rounding of the sums themselves
+                assert (err <= Jb * (1 + 1e-12) + 1e-13 * max(1.0, np.abs(Jf).max())).all(), name
+            if with_k:
+                Kf = np.einsum("ijkl,jl->ik", eri, D[m])
+                err = np.abs(K[m] - Kf)
+                assert (err <= Kb * (1 + 1e-12) + 1e-13 * max(1.0, np.abs(Kf).max())).all(), name
+        # and the rule is not vacuous: at 1e-4 the dropped quartets matter
+        if cutoff == 1e-4 and with_j:
+            Jf = np.einsum("ijkl,kl->ij", eri, D[0])
+            assert np.abs(J[0] - Jf).max() > 1e-9, name
