@@ -36,8 +36,13 @@
  * Errors
  *   Every call returns JK_OK or an error code; jk_last_error() gives a
  *   message for the calling thread. No call aborts the process, traps on the
- *   GPU or throws across the ABI. Device-side waits are bounded and report
- *   JK_ERR_TIMEOUT through the device error word.
+ *   GPU or throws across the ABI. The kernels report a non-finite density
+ *   element through a device error word: a build with stats checks it
+ *   before returning; a build without stats queues a copy of it on the
+ *   stream, and the next call on the handle (jk_build*, jk_check,
+ *   jk_destroy) that finds the copy landed returns JK_ERR_NAN. No kernel of
+ *   the library waits on another kernel or on the host, so JK_ERR_TIMEOUT is
+ *   reserved and returned by no call.
  */
 #ifndef JK_H
 #define JK_H
@@ -55,7 +60,7 @@ enum {
     JK_ERR_UNSUPPORTED = 2,  /* l > JK_LMAX, nprim > JK_NPRIM_MAX, n_dm > JK_NDM_MAX */
     JK_ERR_CUDA = 3,         /* a CUDA runtime or driver call failed */
     JK_ERR_OOM = 4,          /* device allocation failed or above the memory cap */
-    JK_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+    JK_ERR_TIMEOUT = 5,      /* reserved: no call returns it (no device-side waits) */
     JK_ERR_NAN = 6,          /* non-finite density or result detected */
     JK_ERR_COMPILE = 7       /* runtime kernel compilation failed */
 };
@@ -130,7 +135,11 @@ typedef struct {
 
 typedef struct jk_handle jk_handle;
 
-/* One molecule. shells: nshell records (host); coords: natm x 3 (host,
+/* One molecule: the dynamic inputs of Table 2 of the paper (coordinates,
+ * exponents, contraction coefficients) grouped into shells whose (l, nprim)
+ * are the static parameters of Table 1. Builds the shell-pair data that
+ * Sec. 3 says may be precomputed, and the shell-level Schwarz factors of
+ * eq:schwartz. shells: nshell records (host); coords: natm x 3 (host,
  * bohr); exps, coeffs: nprim_total (host). On success *out owns a new
  * handle. Errors: JK_ERR_ARG (NULL, negative sizes, shell fields out of
  * range), JK_ERR_UNSUPPORTED (l or nprim above the limits), JK_ERR_CUDA,
@@ -199,9 +208,16 @@ int jk_info(jk_handle *h, int32_t mol, int32_t *nao, int32_t *nshell, int32_t *n
  * (zero for pairs dropped at init). */
 int jk_schwarz(jk_handle *h, double *Q_host);
 
-/* Synchronises the device, then frees everything the handle owns (device
+/* Synchronises `stream` and reports the device error word of the builds
+ * enqueued on this handle so far (JK_ERR_NAN for a non-finite density
+ * element), clearing it. The asynchronous counterpart of passing stats. */
+int jk_check(jk_handle *h, void *stream);
+
+/* Releases a handle (resource management; no passage of the paper).
+ * Synchronises the device, then frees everything the handle owns (device
  * tables and scratch, captured graphs, streams, events); the caller's D, J
- * and K are untouched. JK_ERR_ARG for NULL. */
+ * and K are untouched. JK_ERR_ARG for NULL; JK_ERR_NAN (after freeing) when
+ * a build whose error word nobody looked at saw a non-finite density. */
 int jk_destroy(jk_handle *h);
 
 /* Router training data from a full FP64 build (which it also returns in J,
@@ -229,28 +245,35 @@ int jk_router_gradient(const jk_router_blob *w, const float *X, const float *y, 
 
 /* The same result as jk_router_gradient (mean pinball loss and gradient over
  * n rows; X, y on the device; grad_host and loss on the host), from a variant
- * that makes no device allocation. The paper has no counterpart; this is for
- * callers that cannot call cudaMalloc: code running while a CUDA stream is
- * being captured (where cudaMalloc is not allowed), and applications that
- * hand every byte of device memory to their own allocator and forbid
- * libraries from allocating more.
+ * that makes no device allocation. The paper has no counterpart. It is for
+ * callers that must not call cudaMalloc: applications whose own allocator
+ * (a framework's caching pool, a server that reserves the GPU's memory at
+ * start-up) owns every byte of device memory and forbids libraries to take
+ * more, and training loops that cannot afford cudaMalloc / cudaFree in the
+ * step (cudaFree synchronises the whole device).
  *   - Scratch: one fixed __device__ array in the library (about 560 KB,
  *     present on every GPU that loads the library until the process exits),
  *     holding the weight copies, the row list and the accumulators. At most
  *     JK_NOALLOC_MAX_ROWS rows per call; larger n returns JK_ERR_UNSUPPORTED
  *     and touches nothing.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     process; make that first call before any stream capture. The kept
+ *     address does not survive cudaDeviceReset: do not call this after one.
  *   - Every call shares the array and clears the accumulators itself; calls
  *     whose work overlaps on the GPU (other streams, other host threads)
- *     race on it. Work is queued on `stream` and the call returns after
- *     synchronising it. */
+ *     race on it. Work is queued on `stream`; the call synchronises `stream`
+ *     and returns with grad_host and loss filled. */
 #define JK_NOALLOC_MAX_ROWS 65536
 int jk_router_gradient_noalloc(const jk_router_blob *w, const float *X, const float *y, int64_t n, float quantile,
                                float *grad_host, double *loss, void *stream);
 
-/* Install router weights on a handle (enables JK_PREC_MIXED_ROUTED). */
+/* Install router weights on a handle (enables JK_PREC_MIXED_ROUTED). The
+ * router extends the Schwarz-based FP32/FP64 split that Sec. 6 of the paper
+ * leaves as future work; the paper itself has no learned router. The blob is
+ * copied (BF16-rounded, in MMA fragment order) to the device; the caller
+ * keeps it. JK_ERR_ARG for a NULL handle or a blob with a wrong magic or
+ * version, JK_ERR_NAN for non-finite weights. */
 int jk_router_load(jk_handle *h, const jk_router_blob *w);
 
 /* After a build with option "profile" = 1 and non-NULL stats: copies up to

@@ -723,6 +723,9 @@ struct jk_handle {
     unsigned long long *d_work = nullptr;  // one counter per launch
     unsigned long long *d_stats = nullptr; // two per launch
     int *d_err = nullptr;
+    int *h_err = nullptr;                  // pinned copy of d_err taken after each build without stats
+    cudaEvent_t err_ev = nullptr;          // recorded after that copy
+    bool err_pending = false;              // a copy is in flight and not yet looked at
     long long *d_tile_off = nullptr;
     long long ntiles = 0;
     long long dmax_total = 0;
@@ -783,6 +786,8 @@ void free_handle(jk_handle *h)
     cudaFree(h->d_dmax); cudaFree(h->d_dmax32); cudaFree(h->d_dmax_mol); cudaFree(h->d_rys64); cudaFree(h->d_rys32);
     cudaFree(h->d_work); cudaFree(h->d_stats); cudaFree(h->d_err); cudaFree(h->d_tile_off);
     if (h->h_mols) cudaFreeHost(h->h_mols);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->err_ev) cudaEventDestroy(h->err_ev);
     if (h->mol_copied) cudaEventDestroy(h->mol_copied);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -1248,6 +1253,9 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
         CK(cudaMallocHost(&h->h_sph, sizeof(JkSphMol) * 2 * nmol));
     }
     CK(cudaMallocHost(&h->h_mols, sizeof(JkMol) * nmol));
+    CK(cudaMallocHost(&h->h_err, sizeof(int)));
+    *h->h_err = 0;
+    CK(cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->mol_copied, cudaEventDisableTiming));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
@@ -1267,6 +1275,29 @@ struct LogSpec {
     float *x, *y;
     long long cap;
 };
+
+// The device error word (set by the kernels: a non-finite density element)
+// as a status: clears the word and returns the matching error code.
+int device_error(jk_handle *h, int err, const char *when)
+{
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    *h->h_err = 0;
+    if (err & JK_ERR_DEV_NAN) return fail(JK_ERR_NAN, "%s: the density holds NaN or infinite values", when);
+    return fail(JK_ERR_CUDA, "%s: device error word %d", when, err);
+}
+
+// A build without stats leaves an asynchronous copy of the error word; look
+// at it if it has landed (the next build, jk_check and jk_destroy do).
+int poll_device_error(jk_handle *h, bool wait)
+{
+    if (!h->err_pending) return JK_OK;
+    cudaError_t q = wait ? cudaEventSynchronize(h->err_ev) : cudaEventQuery(h->err_ev);
+    if (q == cudaErrorNotReady) { cudaGetLastError(); return JK_OK; }
+    CK(q);
+    h->err_pending = false;
+    if (*h->h_err) return device_error(h, *h->h_err, "an earlier build on this handle");
+    return JK_OK;
+}
 
 int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int with_k, double cutoff,
                int mode, double *const *J, double *const *K, void *stream, jk_stats *stats,
@@ -1293,6 +1324,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
     CK(cudaGetDevice(&dev));
     if (dev != h->device) return fail(JK_ERR_ARG, "current device %d differs from the handle's %d", dev, h->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (int prc = poll_device_error(h, false)) return prc;
 
     // kernels for this combination
     std::vector<KSpec> specs;
@@ -1612,11 +1644,14 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             }
         }
         stats->quartets_routed = routed_fp32;
-        if (err) {
-            CK(cudaMemset(h->d_err, 0, sizeof(int)));
-            if (err & JK_ERR_DEV_NAN) return fail(JK_ERR_NAN, "the density holds NaN or infinite values");
-            return fail(err == JK_ERR_DEV_TIMEOUT ? JK_ERR_TIMEOUT : JK_ERR_CUDA, "device error word %d", err);
-        }
+        h->err_pending = false;
+        if (err) return device_error(h, err, "this build");
+    } else {
+        // no synchronisation here: the error word travels back with the
+        // stream and is looked at by the next call on the handle
+        CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(h->err_ev, st));
+        h->err_pending = true;
     }
     return JK_OK;
 }
@@ -1692,7 +1727,8 @@ void *g_noalloc_ptr[64] = {};
 
 // Device address of the scratch array on the current device. Host code may
 // not use the array's name as an address, so it is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and kept for the process (a cudaDeviceReset
+// would invalidate it; the header says so).
 int noalloc_scratch(JkNoAllocScratch **out)
 {
     int dev = 0;
@@ -1993,11 +2029,29 @@ int jk_schwarz(jk_handle *h, double *Q)
     return JK_OK;
 }
 
+int jk_check(jk_handle *h, void *stream)
+{
+    if (!h) return fail(JK_ERR_ARG, "handle is NULL");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    h->err_pending = false;
+    int err = 0;
+    CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return device_error(h, err, "a build on this handle");
+    return JK_OK;
+}
+
 int jk_destroy(jk_handle *h)
 {
     if (!h) return fail(JK_ERR_ARG, "handle is NULL");
     cudaDeviceSynchronize();
+    int err = 0;
+    if (h->d_err && cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        err = 0;
+    }
     free_handle(h);
+    if (err & JK_ERR_DEV_NAN)
+        return fail(JK_ERR_NAN, "a build on the destroyed handle saw NaN or infinite density values");
     return JK_OK;
 }
 

@@ -112,6 +112,6 @@ struct JkSchwarzArgs {
     int npair;
 };
 
-#define JK_ERR_DEV_TIMEOUT 1
-#define JK_ERR_DEV_BOUNDS 2
+// Bits of the device error word. Only the density check sets one today; no
+// kernel of the library waits on another kernel or on the host.
 #define JK_ERR_DEV_NAN 4

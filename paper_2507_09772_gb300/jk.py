@@ -24,7 +24,7 @@ PRECISION = {"fp64": JK_PREC_FP64, "mixed": JK_PREC_MIXED, "routed": JK_PREC_MIX
 
 # every function include/jk.h declares
 EXPORTED = ["jk_init", "jk_init_batch", "jk_build", "jk_build_batch", "jk_set_option",
-            "jk_get_option", "jk_info", "jk_schwarz", "jk_destroy", "jk_router_collect", "jk_router_train",
+            "jk_get_option", "jk_info", "jk_schwarz", "jk_check", "jk_destroy", "jk_router_collect", "jk_router_train",
             "jk_router_forward", "jk_router_gradient", "jk_router_gradient_noalloc", "jk_router_load",
             "jk_profile", "jk_measure_peak",
             "jk_compile_class", "jk_compile_basis", "jk_autotune", "jk_fragment_candidates",
@@ -129,6 +129,7 @@ def load_library() -> ctypes.CDLL:
     lib.jk_info.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     lib.jk_schwarz.argtypes = [vp, dp]
     lib.jk_destroy.argtypes = [vp]
+    lib.jk_check.argtypes = [vp, vp]
     lib.jk_compile_class.argtypes = [i32] * 14 + [P(i32), dp]
     lib.jk_profile.argtypes = [vp, P(JkLaunchProf), i32, P(i32)]
     lib.jk_compile_basis.argtypes = [P(JkShell), i32, i32, i32, i32, i32, i32, dp, P(i32)]
@@ -254,6 +255,12 @@ def jk_schwarz(h) -> np.ndarray:
     q = np.zeros((nsh, nsh))
     _check(load_library().jk_schwarz(h, _dptr(q)))
     return q
+
+
+def jk_check(h, stream=None):
+    """Synchronise the stream and raise if a build on the handle saw a
+    non-finite density (the device error word)."""
+    _check(load_library().jk_check(h, _stream_ptr(stream)))
 
 
 def jk_destroy(h):
@@ -412,9 +419,12 @@ class JK:
         jk_router_load(self.h, blob)
 
     def build(self, D, with_j=True, with_k=True, cutoff=1e-13, precision="fp64", J=None, K=None,
-              stream=None, stats=False):
+              stream=None, stats=False, check=True):
         """D: torch float64 CUDA tensor (n_dm, nao, nao), or a list for batches.
-        Returns (J, K, stats-or-None); J/K allocated with torch if not given."""
+        Returns (J, K, stats-or-None); J/K allocated with torch if not given.
+        With check (the default) a build without stats synchronises the
+        stream and raises on a non-finite density (jk_check); check=False
+        leaves the build asynchronous (the next call on the handle reports)."""
         import torch
         mode = PRECISION[precision] if isinstance(precision, str) else int(precision)
         Dl = list(D) if isinstance(D, (list, tuple)) else [D]
@@ -430,11 +440,15 @@ class JK:
             Kl = K if isinstance(K, list) else [K]
             st = jk_build(self.h, Dl[0], ndm, with_j, with_k, cutoff, mode,
                           Jl[0] if with_j else None, Kl[0] if with_k else None, stream, stats)
+            if check and not stats:
+                jk_check(self.h, stream)
             if listed:
                 return (Jl if with_j else None), (Kl if with_k else None), st
             return (Jl[0] if with_j else None), (Kl[0] if with_k else None), st
         st = jk_build_batch(self.h, Dl, ndm, with_j, with_k, cutoff, mode,
                             J if with_j else None, K if with_k else None, stream, stats)
+        if check and not stats:
+            jk_check(self.h, stream)
         return J, K, st
 
     def autotune(self, D, with_j=True, with_k=True, cutoff=1e-13, precision="fp64", max_candidates=4,

@@ -350,6 +350,13 @@ def test_incremental_density_build_screens_on_the_change():
     J2, K2, s2 = gpu_jk(mol, D=D2, cutoff=1e-13)
     assert np.abs(J1 + Jd - J2).max() <= 1e-10
     assert np.abs(K1 + Kd - K2).max() <= 1e-10
+    # the increment itself against the oracle, screened the same way by
+    # |Delta D| (the values are ~1e-8, so the bound is far below TOL64; a
+    # quartet within rounding of the cutoff changes J or K by < 1e-13 N_f^2)
+    Jr, Kr, nr = oracle.jk(mol, D=D2 - D1, cutoff=1e-13)
+    assert np.abs(Jd - Jr).max() <= 1e-11 and np.abs(Kd - Kr).max() <= 1e-11
+    assert np.abs(Jd).max() > 1e-9   # the comparison is not vacuous
+    assert abs(sd["quartets_fp64"] - nr) <= max(2, 1e-4 * nr)
     # a random density does not decay with distance, so most of the 12-atom
     # molecule's quartets stay above 1e-13 even at |Delta D| ~ 1e-8
     assert sd["quartets_fp64"] < 0.75 * s2["quartets_fp64"]
@@ -378,6 +385,17 @@ def test_non_finite_density_is_reported_and_the_handle_recovers():
     assert e.value.code == jk.JK_ERR_NAN
     J, K, _ = eng.build(D, stats=True)
     torch.cuda.synchronize()
+    # without stats: the binding's default check synchronises and raises
+    with pytest.raises(jk.JKError) as e:
+        eng.build(Dbad)
+    assert e.value.code == jk.JK_ERR_NAN
+    # fully asynchronous: the next call on the handle reports it
+    eng.build(Dbad, check=False)
+    torch.cuda.synchronize()
+    with pytest.raises(jk.JKError) as e:
+        eng.build(D)
+    assert e.value.code == jk.JK_ERR_NAN
+    J, K, _ = eng.build(D)
     eng.close()
     Jr, Kr, _ = oracle.jk(mol)
     assert maxdiff(J.cpu().numpy(), Jr) <= TOL64

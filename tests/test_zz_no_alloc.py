@@ -1,8 +1,9 @@
 """The allocation-free gradient entry point (jk_router_gradient_noalloc).
 
-Callers that cannot call cudaMalloc (code running during CUDA stream
-capture, or applications whose own allocator owns all device memory) use
-this variant; its scratch is a fixed array inside the library. It must give
+Callers that must not call cudaMalloc (applications whose own allocator
+owns all device memory, or loops that cannot afford the device-wide
+synchronisation of cudaFree) use this variant; its scratch is a fixed array
+inside the library. It must give
 the same loss and gradient as jk_router_gradient, call after call, even
 though every call reuses the same scratch. This file is collected last so a
 stop-at-first-failure run has executed every other test before it.
