@@ -40,30 +40,77 @@ WORKLOAD = "batched-631gs-64mol"
 PEAK_FP64_NOMINAL = 152 * 4 * 2.07e9
 PEAK_FP32_NOMINAL = 152 * 256 * 2.07e9
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the largest class kernels, from one ncu capture of the 8-molecule case
-# (`bench.py --nmol 8 ... --tune 0`, heuristic fragment shapes), scaled to
-# the 64-molecule launch by its quartet count. Valid only for the kernel
-# sources they were taken with (hash below) and the same threads per
-# quartet; otherwise the roofline reports traffic null.
+# DRAM traffic of the integral kernel family (dram__bytes_read.sum +
+# dram__bytes_write.sum summed over every jk_class_kernel launch of one
+# build), from one ncu capture of the 8-molecule case of the batched workload
+# (`bench.py --nmol 8 ... --tune 0`, heuristic fragment shapes), per
+# significant quartet of that build, per tier; scaled to a step by its quartet
+# count. Valid only for the kernel sources it was taken with (hash below);
+# otherwise the roofline reports traffic null.
 TRAFFIC_SOURCES = ["paper_2507_09772_gb300/csrc/jk_kernels.cuh", "paper_2507_09772_gb300/csrc/jk_types.h",
-                   "paper_2507_09772_gb300/csrc/jk_router.cuh", "paper_2507_09772_gb300/csrc/jk_api.cu"]
-TRAFFIC_SHA = "d5369a7d5ce253e1"
-TRAFFIC_BYTES = {   # (kernel label, threads per quartet): bytes per full-size launch
-    ("jk_class_kernel<(21|10) prims 1113, fp64>", 2): 13381376 * 20995695 / 2141233,
-    ("jk_class_kernel<(11|11) prims 3111, fp64>", 3): 3046400 * 12299763 / 1246899,
-}
+                   "paper_2507_09772_gb300/csrc/jk_router.cuh"]
+TRAFFIC_SHA = None                   # kernel sources of the capture below
+TRAFFIC_BYTES_PER_QUARTET = {}       # tier (0 FP64, 1 FP32) -> DRAM bytes per significant quartet
 
 
-def traffic_for(label, g):
+def sources_sha():
     import hashlib
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest()[:16] != TRAFFIC_SHA:
+    return h.hexdigest()[:16]
+
+
+def traffic_for(tier, quartets):
+    """DRAM bytes of the class kernels of one tier for `quartets` quartets, or
+    None when no capture of the current kernel sources exists."""
+    if TRAFFIC_SHA is None or tier not in TRAFFIC_BYTES_PER_QUARTET or sources_sha() != TRAFFIC_SHA:
         return None
-    return TRAFFIC_BYTES.get((label, g))
+    return TRAFFIC_BYTES_PER_QUARTET[tier] * quartets
+
+
+def family_roofline(prof_rows, tier, probe, ms_serial):
+    """Roofline of one tier's integral kernels taken as one kernel family
+    (every class instantiation of jk_class_kernel): modelled FLOPs of the
+    quartets they evaluated over their summed serialised launch times, which
+    is the FLOPs per launch over the average launch duration. The work is
+    spread over hundreds of class kernels (none above 2 % of the step), so the
+    family, not one class, is the dominant kernel."""
+    rows = [v for v in prof_rows if v["tier"] == tier]
+    if not rows:
+        return None
+    ms = sum(v["ms"] for v in rows)
+    fl = sum(v["flops_model"] for v in rows)
+    q = sum(v["quartets"] for v in rows)
+    n = sum(v["launches"] for v in rows)
+    peak = PEAK_FP64_NOMINAL if tier == 0 else PEAK_FP32_NOMINAL
+    ach = fl / (ms * 1e-3) if ms > 0 else 0.0
+    dom = max(rows, key=lambda v: v["ms"])
+    traffic = traffic_for(tier, q)
+    return {
+        "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+        "traffic": traffic / n if traffic is not None else None,
+        "traffic_note": ("DRAM bytes per launch (family average) from an 8-molecule ncu capture, per quartet, "
+                         "scaled by this step's quartets: %.1f GB/s over the launches"
+                         % (traffic / (ms * 1e-3) / 1e9)) if traffic is not None else None,
+        "kernel": "jk_class_kernel<..., %s> (all %d class instantiations of the tier)"
+                  % ("double" if tier == 0 else "float", n),
+        "launches": n, "launch_ms": ms / n, "kernel_ms": ms,
+        "kernel_share": ms / ms_serial if ms_serial else None,
+        "flops_per_launch": fl / n,
+        "timing": "CUDA events around each launch, serialised replay after the timed region",
+        "peak_source": ("nominal FP64 FMA rate: 152 SMs x 4 FLOP/clk x 2.07 GHz (MEASURED_PEAKS.json has no FP64 "
+                        "figure)" if tier == 0 else
+                        "nominal FP32 FMA rate: 152 SMs x 256 FLOP/clk x 2.07 GHz (MEASURED_PEAKS.json has no FP32 "
+                        "figure)"),
+        "peak_probe_tflops": probe / 1e12 if probe else None,
+        "frac_of_probe": ach / probe if probe else None,
+        "largest_class": {"class": "(%d%d|%d%d)/%d%d%d%d" % (dom["la"], dom["lb"], dom["lc"], dom["ld"], dom["na"],
+                                                              dom["nb"], dom["nc"], dom["nd"]),
+                          "share_of_tier": dom["ms"] / ms, "tflops_model": dom["flops_model"] / (dom["ms"] * 1e-3) / 1e12,
+                          "G": dom["threads_per_quartet"], "regs": dom["regs"]},
+    }
 
 
 def parse():
@@ -82,13 +129,21 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--oracle-sample", type=int, default=ORACLE_SAMPLE,
+                    help="smallest molecules of the batch in the oracle's sample (cpu_baseline and --impl reference)")
     ap.add_argument("--no-probe", action="store_true", help="skip the FMA peak probes (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
+    ap.add_argument("--forms", default="mixed,routed", help="accelerated forms timed against the FP64 build")
+    ap.add_argument("--chunk", type=int, default=0, help="candidate kets per work item (0: the library default)")
+    ap.add_argument("--oracle-blocks", type=int, default=8,
+                    help="single large molecules: J and K shell blocks the oracle computes to check every form")
     ap.add_argument("--form-steps", type=int, default=2)
     ap.add_argument("--tau32", type=float, default=1e-4)
     ap.add_argument("--graph", type=int, default=1, help="replay each build as one CUDA graph")
     ap.add_argument("--branches", type=int, default=4, help="class kernels forked over this many graph branches")
     ap.add_argument("--micro", action="store_true", help="appendix-style micro-benchmarks instead of the workload")
+    ap.add_argument("--micro-cases", default="ss,d,f,forms",
+                    help="micro-benchmark parts: ss ((ss|ss) n_prim sweep), d, f (n_dm sweeps), forms (the rest)")
     ap.add_argument("--tune", type=int, default=1, help="autotune the fragment shapes before the warm-up (untimed)")
     ap.add_argument("--prof-steps", type=int, default=1, help="serialised, per-kernel-timed steps after the timed region")
     return ap.parse_args()
@@ -159,9 +214,9 @@ class ClockSampler:
 ORACLE_SAMPLE = 6
 
 
-def oracle_sample(mols):
+def oracle_sample(mols, n=ORACLE_SAMPLE):
     order = sorted(range(len(mols)), key=lambda i: (mols[i].natm, i))
-    return [mols[i] for i in order[:ORACLE_SAMPLE]]
+    return [mols[i] for i in order[:n]]
 
 
 def oracle_pass(sample, cutoff):
@@ -175,7 +230,7 @@ def oracle_pass(sample, cutoff):
     return nq, time.perf_counter() - t0
 
 
-def cpu_oracle_sample(mols, seconds: float, cutoff: float, quartets_per_step=None):
+def cpu_oracle_sample(mols, seconds: float, cutoff: float, quartets_per_step=None, nsample=ORACLE_SAMPLE):
     """Oracle (as it stands) on a bounded sample of the workload on the host
     cores. Batched workload: repeated passes over the same molecules the
     reference arm times, until `seconds` pass. A single large molecule: exact
@@ -201,7 +256,7 @@ def cpu_oracle_sample(mols, seconds: float, cutoff: float, quartets_per_step=Non
                "sample": f"row-restricted: exact J shell blocks of the molecule ({nb} blocks, {nq} shell "
                          f"quartets, {t_total:.1f} s; each screened quartet of a block counted once)"}
     else:
-        sample = oracle_sample(mols)
+        sample = oracle_sample(mols, nsample)
         nq, t_total, passes = 0, 0.0, 0
         while t_total < seconds or passes == 0:
             n, dt = oracle_pass(sample, cutoff)
@@ -226,7 +281,7 @@ def run_reference(args):
     from paper_2507_09772_gb300 import synth
     import oracle
     mols = synth.batched_631gs(args.nmol)
-    sample = oracle_sample(mols)
+    sample = oracle_sample(mols, args.oracle_sample)
     for _ in range(args.warmup):
         oracle_pass(sample, args.cutoff)
     nq = 0
@@ -258,14 +313,20 @@ def tier_split(eng, Ds, Js, Ks, args, precision):
     try:
         eng.set_option("profile", 1)
         eng.set_option("branches", 1)
-        eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)
+        _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)
         ms = {0: 0.0, 1: 0.0}
         q = {0: 0, 1: 0}
+        rows = []
         for p in jk.jk_profile(eng.h):
             ms[p["tier"]] += p["ms"]
             q[p["tier"]] += p["quartets"]
-        return {"fp64_kernels_ms": ms[0], "fp32_kernels_ms": ms[1], "fp64_quartets": q[0], "fp32_quartets": q[1],
-                "timing": "serialised replay, CUDA events around each class launch"}
+            rows.append(dict(p, launches=1))
+        out = {"fp64_kernels_ms": ms[0], "fp32_kernels_ms": ms[1], "fp64_quartets": q[0], "fp32_quartets": q[1],
+               "serial_build_ms": st["ms"], "timing": "serialised replay, CUDA events around each class launch"}
+        probes = {0: getattr(args, "probe64", None), 1: getattr(args, "probe32", None)}
+        for t, name in ((0, "fp64_tier_roofline"), (1, "fp32_tier_roofline")):
+            out[name] = family_roofline(rows, t, probes[t], st["ms"])
+        return out
     except Exception as e:   # a diagnostic, never the reason a run fails
         return {"error": str(e)[:200]}
     finally:
@@ -273,18 +334,60 @@ def tier_split(eng, Ds, Js, Ks, args, precision):
         eng.set_option("branches", args.branches)
 
 
-def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets):
-    """Mixed (Schwarz x Dmax tiering) and routed (learned router in the band)
-    builds of the same batch, timed like the FP64 steps, with their largest
-    deviation from the FP64 result over every element of J and K."""
+def oracle_blocks(mol, nblocks, cutoff, seed=7):
+    """Exact J and K shell blocks of one large Cartesian molecule from the CPU
+    oracle (row-restricted: J_ab and K_ac straight from eq:jk), half of them
+    on nearby shell pairs (the blocks that carry J), half uniform. Returns a
+    function that gives max |dJ|, max |dK| of a GPU result on those blocks."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    xyz = np.asarray(mol.coords)[mol.shells[:, 0]]
+
+    def pairs(n):
+        out = []
+        for i in range(n):
+            a = int(rng.integers(mol.nshell))
+            if i < n // 2:
+                near = np.nonzero(np.linalg.norm(xyz - xyz[a], axis=1) < 2.5)[0]
+                out.append((a, int(rng.choice(near))))
+            else:
+                out.append((a, int(rng.integers(mol.nshell))))
+        return np.array(out, dtype=np.int64)
+    jb, kb = pairs(nblocks), pairs(nblocks)
+    t0 = time.perf_counter()
+    Jl, Kl, nq = oracle.jk_blocks(mol, jb, kb, cutoff=cutoff)
+    secs = time.perf_counter() - t0
+    off = np.cumsum([0] + [oracle.ncart(int(l)) for l in mol.shells[:, 1]])
+
+    def compare(J, K):
+        J = J.cpu().numpy()[0] if hasattr(J, "cpu") else J[0]
+        K = K.cpu().numpy()[0] if hasattr(K, "cpu") else K[0]
+        dj = max(float(np.abs(J[off[a]:off[a + 1], off[b]:off[b + 1]] - blk[0]).max()) for (a, b), blk in zip(jb, Jl))
+        dk = max(float(np.abs(K[off[a]:off[a + 1], off[c]:off[c + 1]] - blk[0]).max()) for (a, c), blk in zip(kb, Kl))
+        return {"max_abs_dJ_oracle": dj, "max_abs_dK_oracle": dk}
+    info = {"blocks": f"{nblocks} J and {nblocks} K shell blocks (half on pairs within 2.5 bohr)",
+            "oracle_quartets": int(nq), "oracle_s": secs, "cores": oracle.num_threads()}
+    return compare, info
+
+
+def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets, ocmp=None):
+    """The accelerated forms listed in --forms (mixed: Schwarz x Dmax tiering;
+    mixed_asym64, mixed_screen64: the same with the FP32 tier's large-T Rys
+    limit, or every bound, in FP64; routed: the learned router in the band)
+    on the same inputs, timed like the base build (--precision), with their
+    largest deviation from the base build over every element of J and K (and,
+    for a single large molecule, from the oracle on sampled shell blocks)."""
     import torch
     from paper_2507_09772_gb300 import jk
 
+    base = args.precision
+    forms = [f for f in args.forms.split(",") if f and f != base]
     Jref = [j.clone() for j in Js]
     Kref = [k.clone() for k in Ks]
     eng.set_option("tau32", args.tau32)
-    out = {"fp64": {"ms_per_step": fp64_ms, "quartets_per_s": fp64_quartets / (fp64_ms * 1e-3)},
-           "tau32": args.tau32, "accuracy_reference": "the FP64 build of this run (full matrices)"}
+    out = {base: {"ms_per_step": base_ms, "quartets_per_s": base_quartets / (base_ms * 1e-3)},
+           "tau32": args.tau32, "accuracy_reference": f"the {base} build of this run (full matrices)"}
 
     def timed(precision):
         _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)  # warm
@@ -304,43 +407,63 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, fp64_ms, fp64_quartets
         dk = max(float((a - b).abs().max()) for a, b in zip(Ks, Kref))
         st = sts[-1]
         q = st["quartets_fp64"] + st["quartets_fp32"]
-        return {"ms_per_step": ms, "quartets_per_s": q / (ms * 1e-3), "speedup_vs_fp64": fp64_ms / ms,
-                "max_abs_dJ": dj, "max_abs_dK": dk, "within_1e-8": bool(max(dj, dk) <= 1e-8),
-                "fp32_fraction": st["quartets_fp32"] / max(1, q), "quartets_routed": st["quartets_routed"],
-                "same_quartets_as_fp64": bool(q == fp64_quartets)}
+        r = {"ms_per_step": ms, "quartets_per_s": q / (ms * 1e-3), f"speedup_vs_{base}": base_ms / ms,
+             "max_abs_dJ": dj, "max_abs_dK": dk, "within_1e-8": bool(max(dj, dk) <= 1e-8),
+             "fp32_fraction": st["quartets_fp32"] / max(1, q), "quartets_fp64": st["quartets_fp64"],
+             "quartets_fp32": st["quartets_fp32"], "quartets_routed": st["quartets_routed"],
+             f"same_quartets_as_{base}": bool(q == base_quartets)}
+        if ocmp is not None:
+            r.update(ocmp(Js[0], Ks[0]))
+        return r
 
-    # the FP32 tier's shapes, tuned on all-FP32 builds (93% of the mixed quartets are FP32)
-    tune = (eng.autotune(Ds, cutoff=args.cutoff, precision="fp32", max_candidates=3, min_share=0.01)
-            if args.tune else None)
-    out["mixed"] = timed("mixed")
-    out["mixed"]["autotune"] = tune
-    out["mixed"]["tiers"] = tier_split(eng, Ds, Js, Ks, args, "mixed")
-    # router: labels from FP64 logging builds of held-out molecules shaped
-    # like the batched and cluster workloads (not the ones timed here),
-    # trained on the GPU, then routed builds of the workload
-    t0 = time.perf_counter()
-    from paper_2507_09772_gb300 import synth
-    sub = synth.batched_631gs(6, seed_base=5001) + [synth.water_like_cluster(64, seed=5002)]
-    eng_l = jk.JK(sub)
-    eng_l.set_option("tau32", args.tau32)
-    Dl = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in sub]
-    Jl = [torch.empty_like(d) for d in Dl]
-    Kl = [torch.empty_like(d) for d in Dl]
-    cap = 2_000_000
-    X = torch.empty((cap, 12), dtype=torch.float32, device="cuda")
-    y = torch.empty(cap, dtype=torch.float32, device="cuda")
-    n = min(cap, jk.jk_router_collect(eng_l.h, Dl, 1, args.cutoff, Jl, Kl, X, y))
-    eng_l.close()
-    blob, tst = jk.jk_router_train(X[:n], y[:n], steps=1500, batch=8192, lr=2e-3, quantile=0.95, seed=1)
-    train_s = time.perf_counter() - t0
-    eng.load_router(blob)
-    r = timed("routed")
-    r["tiers"] = tier_split(eng, Ds, Js, Ks, args, "routed")
-    r.update({"train_samples": int(n), "train_s": train_s, "train_loss_first": tst["loss_first"],
-              "train_loss_last": tst["loss_last"],
-              "train_set": "FP64 labels of 6 held-out batch molecules and a 64-unit cluster"})
-    out["routed"] = r
-    # leave the FP64 result in Js, Ks
+    if "mixed" in forms:
+        # the FP32 tier's shapes, tuned on all-FP32 builds (most mixed quartets are FP32)
+        tune = (eng.autotune(Ds, cutoff=args.cutoff, precision="fp32", max_candidates=3, min_share=0.01)
+                if args.tune else None)
+        out["mixed"] = timed("mixed")
+        out["mixed"]["autotune"] = tune
+        out["mixed"]["tiers"] = tier_split(eng, Ds, Js, Ks, args, "mixed")
+    # the mixed build with the large-T Rys limit of the FP32 tier in FP64
+    # (asym64) and with every bound compared in FP64 (screen64)
+    ref_mixed = out["mixed"]["ms_per_step"] if "mixed" in out else (base_ms if base == "mixed" else None)
+    for name, opt in (("mixed_asym64", "asym64"), ("mixed_screen64", "screen64")):
+        if name in forms:
+            eng.set_option(opt, 1)
+            try:
+                out[name] = timed("mixed")
+                if ref_mixed:
+                    out[name]["cost_vs_mixed"] = out[name]["ms_per_step"] / ref_mixed - 1.0
+            finally:
+                eng.set_option(opt, 0)
+    if "routed" in forms:
+        # router: labels from FP64 logging builds of held-out molecules shaped
+        # like the batched and cluster workloads (not the ones timed here),
+        # trained on the GPU, then routed builds of the workload
+        t0 = time.perf_counter()
+        from paper_2507_09772_gb300 import synth
+        sub = synth.batched_631gs(6, seed_base=5001) + [synth.water_like_cluster(64, seed=5002)]
+        eng_l = jk.JK(sub)
+        eng_l.set_option("tau32", args.tau32)
+        Dl = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in sub]
+        Jl = [torch.empty_like(d) for d in Dl]
+        Kl = [torch.empty_like(d) for d in Dl]
+        cap = 2_000_000
+        X = torch.empty((cap, 12), dtype=torch.float32, device="cuda")
+        y = torch.empty(cap, dtype=torch.float32, device="cuda")
+        n = min(cap, jk.jk_router_collect(eng_l.h, Dl, 1, args.cutoff, Jl, Kl, X, y))
+        eng_l.close()
+        blob, tst = jk.jk_router_train(X[:n], y[:n], steps=1500, batch=8192, lr=2e-3, quantile=0.95, seed=1)
+        train_s = time.perf_counter() - t0
+        eng.load_router(blob)
+        r = timed("routed")
+        r["tiers"] = tier_split(eng, Ds, Js, Ks, args, "routed")
+        r.update({"train_samples": int(n), "train_s": train_s, "train_loss_first": tst["loss_first"],
+                  "train_loss_last": tst["loss_last"],
+                  "train_set": "FP64 labels of 6 held-out batch molecules and a 64-unit cluster"})
+        if ref_mixed:
+            r["speedup_vs_mixed"] = ref_mixed / r["ms_per_step"]
+        out["routed"] = r
+    # leave the base result in Js, Ks
     for a, b in zip(Js, Jref):
         a.copy_(b)
     for a, b in zip(Ks, Kref):
@@ -378,6 +501,8 @@ def run_ours(args):
     init_s = time.perf_counter() - t0
     eng.set_option("use_graph", args.graph)
     eng.set_option("branches", args.branches)
+    if args.chunk:
+        eng.set_option("chunk", args.chunk)
     Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
     Js = [torch.empty_like(d) for d in Ds]
     Ks = [torch.empty_like(d) for d in Ds]
@@ -448,32 +573,15 @@ def run_ours(args):
         ms_max, q_all = ms_total, float(quartets)
     value = q_all / (ms_max * 1e-3)
 
-    # dominant integral kernel and its roofline (FP64 or FP32 FMA pipe)
+    # roofline of the integral kernel family (FP64 FMA pipe)
+    args.probe64 = None if args.no_probe else jk.jk_measure_peak("fp64", 100.0)
+    args.probe32 = None if args.no_probe else jk.jk_measure_peak("fp32", 100.0)
+    tier = 0 if args.precision == "fp64" else 1
+    roofline = family_roofline(list(prof.values()), tier, args.probe64 if tier == 0 else args.probe32,
+                               ms_serial / args.prof_steps)
+    if args.precision == "mixed":
+        roofline["fp64_tier"] = family_roofline(list(prof.values()), 0, args.probe64, ms_serial / args.prof_steps)
     total_kernel_ms = sum(v["ms"] for v in prof.values())
-    dom = max(prof.values(), key=lambda v: v["ms"])
-    dom_ms = dom["ms"] / dom["launches"]
-    dom_flops = dom["flops_model"] / dom["launches"]
-    peak = PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL
-    probe = (jk.jk_measure_peak("fp64" if dom["tier"] == 0 else "fp32", 100.0) if not args.no_probe
-             else (PEAK_FP64_NOMINAL if dom["tier"] == 0 else PEAK_FP32_NOMINAL))
-    dom_label = "jk_class_kernel<(%d%d|%d%d) prims %d%d%d%d, %s>" % (
-        dom["la"], dom["lb"], dom["lc"], dom["ld"], dom["na"], dom["nb"], dom["nc"], dom["nd"],
-        "fp64" if dom["tier"] == 0 else "fp32")
-    traffic = traffic_for(dom_label, dom["threads_per_quartet"])
-    roofline = {
-        "bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-        "frac": dom_flops / (dom_ms * 1e-3) / peak, "traffic": traffic,
-        "traffic_note": ("DRAM bytes per launch from an 8-molecule ncu capture scaled by quartets; "
-                         "%.2f GB/s over the launch" % (traffic / (dom_ms * 1e-3) / 1e9)) if traffic else None,
-        "kernel": dom_label,
-        "kernel_share": dom["ms"] / ms_serial,
-        "launch_ms": dom_ms, "launches": dom["launches"],
-        "timing": "CUDA events around each launch, serialised replay after the timed region",
-        "peak_source": "nominal FP64 FMA rate: 152 SMs x 4 FLOP/clk x 2.07 GHz" if dom["tier"] == 0
-        else "nominal FP32 FMA rate: 152 SMs x 256 FLOP/clk x 2.07 GHz",
-        "peak_probe_tflops": probe / 1e12, "frac_of_probe": dom_flops / (dom_ms * 1e-3) / probe,
-        "threads_per_quartet": dom["threads_per_quartet"], "regs": dom["regs"], "local_bytes": dom["local_bytes"],
-    }
     all_flops = sum(v["flops_model"] for v in prof.values())
     path_fp64 = {"model_tflops": all_flops / (total_kernel_ms * 1e-3) / 1e12,
                  "frac_of_fp64_peak": all_flops / (total_kernel_ms * 1e-3) / PEAK_FP64_NOMINAL}
@@ -514,14 +622,24 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": t_e / args.steps}
 
+    # a single large Cartesian molecule: sampled oracle blocks for every form
+    ocmp, oinfo, fp64_oracle = None, None, None
+    if args.oracle_blocks > 0 and len(mols) == 1 and mols[0].natm > 100 and not mols[0].spherical and rank == 0:
+        ocmp, oinfo = oracle_blocks(mols[0], args.oracle_blocks, args.cutoff)
+        fp64_oracle = ocmp(Js[0], Ks[0])
+
     # the accelerated forms on the same inputs, against this FP64 build
     forms = None
-    if not args.no_forms and args.precision == "fp64":
-        forms = run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, ms_max / args.steps, quartets / args.steps)
+    if not args.no_forms and args.precision != "fp32":
+        forms = run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, ms_max / args.steps, quartets / args.steps,
+                          ocmp)
+        if fp64_oracle:
+            forms[args.precision].update(fp64_oracle)
+            forms["oracle_blocks"] = oinfo
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_oracle_sample(mols, args.cpu_seconds, args.cutoff, quartets / args.steps)
+        cpu = cpu_oracle_sample(mols, args.cpu_seconds, args.cutoff, quartets / args.steps, args.oracle_sample)
 
     if rank == 0:
         nbf = sum(m.nao for m in mols)
@@ -556,8 +674,8 @@ def run_ours(args):
             "init_ms": 1e3 * init_s,
             "first_build_s": first_s,
             "compile_ms": eng.get_option("compile_ms"),
-            "peak_probe_fp64_tflops": None if args.no_probe else jk.jk_measure_peak("fp64", 100.0) / 1e12,
-            "peak_probe_fp32_tflops": None if args.no_probe else jk.jk_measure_peak("fp32", 100.0) / 1e12,
+            "peak_probe_fp64_tflops": None if args.no_probe else args.probe64 / 1e12,
+            "peak_probe_fp32_tflops": None if args.no_probe else args.probe32 / 1e12,
             "top_kernels": sorted(
                 [{"class": "(%d%d|%d%d)/%d%d%d%d" % (v["la"], v["lb"], v["lc"], v["ld"], v["na"], v["nb"], v["nc"], v["nd"]),
                   "tier": v["tier"], "ms_per_step": v["ms"] / args.prof_steps, "share": v["ms"] / ms_serial,
@@ -601,8 +719,9 @@ def run_micro(args):
         return statistics.median(ms), st
 
     rows = []
+    cases = set(args.micro_cases.split(","))
     xyz = geometry(32, 2001)
-    for n in range(1, 9):
+    for n in (range(1, 9) if "ss" in cases else ()):
         rng = np.random.default_rng(3000 + n)
         exps = np.geomspace(30.0, 0.15, n) if n > 1 else np.array([0.8])
         mol = synth.custom_basis_molecule(xyz, [[(0, exps)] for _ in range(len(xyz))], rng, name=f"s{n}")
@@ -616,6 +735,8 @@ def run_micro(args):
                      "prim_quartets": s64["prim_quartets"]})
     xyz = geometry(64, 2002)
     for l, name in ((2, "d-only"), (3, "f-only")):
+        if name[0] not in cases:
+            continue
         rng = np.random.default_rng(4000 + l)
         per_atom = [[(l, np.array([np.exp(rng.uniform(np.log(0.4), np.log(1.2)))]))] for _ in range(len(xyz))]
         mol = synth.custom_basis_molecule(xyz, per_atom, rng, n_dm=4, name=name)
@@ -631,6 +752,9 @@ def run_micro(args):
         a = np.polyfit([p[0] for p in pts], [p[1] for p in pts], 1)
         rows.append({"case": name, "fit": "ms = integrals + n_dm * per_density",
                      "integrals_ms": float(a[1]), "per_density_ms": float(a[0])})
+    if "forms" not in cases:
+        print(json.dumps({"micro": rows, "cutoff": args.cutoff, "data": "synthetic"}))
+        return
     # the "next" forms on 8 molecules of the batched workload: range
     # separation, J-only / K-only, and an incremental build of a small change
     mols = synth.batched_631gs(8)

@@ -105,6 +105,9 @@ typedef struct {
  * MLP, BF16 weights in use, FP32 accumulation. It predicts, for a quartet in
  * the band tau32 < B <= K tau32 (B = Q_ab Q_cd Dmax), y = log10(max|T| / (Q_ab
  * Q_cd)), and the quartet runs in FP32 iff log10(B / tau32) + y + margin <= 0.
+ * In a routed build the FP64 tier screens the band and runs the router; the
+ * quartets it releases are evaluated by an FP32 list kernel per class pair,
+ * and the FP32 tier itself keeps the plain Schwarz split (B <= tau32).
  * theta is the FP32 master copy, flat: W1[16][64] b1[64] W2[64][64] b2[64]
  * W3[64] b3 (inputs padded to 16, rows 12..15 unused). The features are
  * normalised as (x - mu) * isd. */
@@ -187,7 +190,17 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * whose sum over the parts is the full result, i.e. one sum all-reduce
  * combines GPUs that split one batch),
  * "branches" (1..8: class kernels forked over this many streams / graph
- * branches). With "use_graph" = 1 the first build of a flag combination is
+ * branches),
+ * "chunk" (32..4096, default 64: candidate kets per work item of the
+ * persistent class kernels; changing it re-plans the work items),
+ * "asym64" (0/1, default 0: the FP32 tier evaluates the large-T
+ * Gauss-Hermite limit of the Rys roots and weights in FP64 and rounds the
+ * result to FP32, instead of evaluating it in FP32),
+ * "screen64" (0/1, default 0: compare the screening bounds, tier thresholds
+ * and the primitive threshold in FP64 whatever the cutoff),
+ * "route_cap" (default 16777216: entries of the per-class-pair lists of
+ * quartets the router releases from the FP64 tier, shared out by estimated
+ * work; a released quartet that finds its list full stays in FP64). With "use_graph" = 1 the first build of a flag combination is
  * captured into a CUDA graph on an internal stream and replayed on `stream`
  * by later builds; the per-call D/J/K pointers are read from a device
  * descriptor copied before each launch, so changing buffers is allowed.
@@ -286,7 +299,9 @@ int jk_measure_peak(int32_t which, double ms, double *flops_per_s);
 
 /* Ahead-of-time compilation of one class kernel (angular momenta la..ld,
  * primitive counts na..nd, n_dm, flags, fp32 = 1 for the FP32 tier, mode 0
- * plain / 1 routed / 2 router-label logging, op 0 1/r / 1 erf / 2 erfc) into
+ * plain / 1 routed FP64 tier (runs the router on its band) / 2 router-label
+ * logging (FP64) / 3 routed FP32 list kernel (the quartets mode 1 released),
+ * op 0 1/r / 1 erf / 2 erfc) into
  * the on-disk kernel cache (JK_KERNEL_CACHE, else next to the library).
  * Needs no GPU. *threads_per_quartet receives the fragmentation chosen.
  * JK_ERR_COMPILE with the NVRTC log in jk_last_error() on failure. */

@@ -575,19 +575,24 @@ long long oracle_jk_rows(const oshell *sh, int nsh, const double *coords, const 
     if (kout) memset(kout, 0, sizeof(double) * kpos[nkblk]);
     long long count = 0;
     int ntask = njblk + nkblk;
+    /* parallel over (block, x): each thread sums into its own copy of the
+     * outputs, added up at the end (only the summation order differs from a
+     * serial loop) */
 #pragma omp parallel reduction(+ : count)
     {
         double *Rbuf = (double *)malloc(sizeof(double) * RD * RD * RD * RD);
         double *blk = (double *)malloc(sizeof(double) * NCMAX * NCMAX * NCMAX * NCMAX);
-#pragma omp for schedule(dynamic, 1)
-        for (int task = 0; task < ntask; ++task) {
-            int isj = task < njblk;
-            int ti = isj ? task : task - njblk;
-            const int *bl = isj ? jblk : kblk;
-            int s1 = bl[2 * ti], s2 = bl[2 * ti + 1];
-            int n1 = ncart(sh[s1].l), n2 = ncart(sh[s2].l);
-            double *dst = isj ? jout + jpos[ti] : kout + kpos[ti];
-            for (int x = 0; x < nsh; ++x)
+        double *jl = (double *)calloc((size_t)jpos[njblk] + 1, sizeof(double));
+        double *kl = (double *)calloc((size_t)kpos[nkblk] + 1, sizeof(double));
+#pragma omp for collapse(2) schedule(dynamic, 1)
+        for (int task = 0; task < ntask; ++task)
+            for (int x = 0; x < nsh; ++x) {
+                int isj = task < njblk;
+                int ti = isj ? task : task - njblk;
+                const int *bl = isj ? jblk : kblk;
+                int s1 = bl[2 * ti], s2 = bl[2 * ti + 1];
+                int n1 = ncart(sh[s1].l), n2 = ncart(sh[s2].l);
+                double *dst = isj ? jl + jpos[ti] : kl + kpos[ti];
                 for (int y = 0; y < nsh; ++y) {
                     int a, b, c, d;
                     if (isj) { a = s1; b = s2; c = x; d = y; }
@@ -612,8 +617,13 @@ long long oracle_jk_rows(const oshell *sh, int nsh, const double *coords, const 
                                     }
                     }
                 }
+            }
+#pragma omp critical
+        {
+            if (jout) for (long long i = 0; i < jpos[njblk]; ++i) jout[i] += jl[i];
+            if (kout) for (long long i = 0; i < kpos[nkblk]; ++i) kout[i] += kl[i];
         }
-        free(Rbuf); free(blk);
+        free(Rbuf); free(blk); free(jl); free(kl);
     }
     free(off); free(jpos); free(kpos);
     return count;

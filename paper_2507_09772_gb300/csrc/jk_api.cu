@@ -138,10 +138,18 @@ struct KSpec {
     // G <= 32: four warps, each holding 32/G groups; G > 32: one group (or
     // one of its gx slabs) per CTA
     int block() const { return G() <= 32 ? 128 : ((G() / gx + 31) / 32) * 32; }
+    // FP32 class kernels keep their N-root Rys table in shared memory
+    size_t rys_table_bytes() const
+    {
+        if (kind != 0 || !fp32) return 0;
+        const int n = (la + lb + lc + ld) / 2 + 1;
+        // per interval 2 n functions x 8 coefficients, padded by 4 floats
+        return (size_t)rys32_nint_host[n] * (2 * n * (rys32_deg_host + 1) + 4) * sizeof(float);
+    }
     size_t smem_bytes() const
     {
         const size_t groups = G() <= 32 ? (size_t)4 * (32 / G()) : 1;
-        return groups * smem_group_reals() * (fp32 ? 4 : 8);
+        return rys_table_bytes() + groups * smem_group_reals() * (fp32 ? 4 : 8);
     }
     int groups_per_cta() const { return G() <= 32 ? 4 * (32 / G()) : 1; }
 };
@@ -184,8 +192,7 @@ std::string cache_dir()
 std::vector<std::string> nvrtc_options(const KSpec &s)
 {
     // No --use_fast_math for the FP32 tier: the pair data already hold every
-    // exponential, and identical compile options in both tiers keep the
-    // router's decisions bit-identical across the FP64 and FP32 kernels.
+    // exponential, and the router's arithmetic stays exactly rounded.
     (void)s;
     return {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
 }
@@ -721,7 +728,7 @@ struct jk_handle {
     double *d_rys64 = nullptr;
     float *d_rys32 = nullptr;
     unsigned long long *d_work = nullptr;  // one counter per launch
-    unsigned long long *d_stats = nullptr; // two per launch
+    unsigned long long *d_stats = nullptr; // three per launch and tier
     int *d_err = nullptr;
     int *h_err = nullptr;                  // pinned copy of d_err taken after each build without stats
     cudaEvent_t err_ev = nullptr;          // recorded after that copy
@@ -747,7 +754,7 @@ struct jk_handle {
     double init_ms = 0, compile_ms = 0;
     std::vector<cudaEvent_t> prof_ev;      // two per launch slot
     std::vector<jk_launch_prof> prof;
-    std::vector<int> prof_slot;            // launch * 2 + tier of each prof record
+    std::vector<int> prof_slot;            // launch * 3 + tier of each prof record
     // spherical molecules: Cartesian scratch copies of D, J, K
     std::vector<char> mol_sph;             // per molecule
     std::vector<int> sh_ao_user;           // molecule-local AO offset in the caller's basis
@@ -766,6 +773,13 @@ struct jk_handle {
     JkRouterDev *d_router = nullptr;
     bool has_router = false;
     unsigned long long *d_logn = nullptr;
+    JkRouted *d_rlist = nullptr;           // routed builds: released quartets, per launch segments
+    unsigned long long *d_rcount = nullptr;
+    std::vector<long long> rl_off, rl_cap;
+    double route_cap = 16777216.0;         // list entries over all launches
+    int asym64 = 0;                        // FP32 tier: large-T roots and weights in FP64
+    int chunk = 64;                        // kets per work item
+    int screen64 = 0;                      // bounds compared in FP64 whatever the cutoff
     // graphs and branch streams
     int branches = 1;
     cudaStream_t cap = nullptr;
@@ -795,6 +809,7 @@ void free_handle(jk_handle *h)
     cudaFree(h->d_sh_l); cudaFree(h->d_sh_sph); cudaFree(h->d_sh_aou); cudaFree(h->d_c2s_off);
     cudaFree(h->d_c2s); cudaFree(h->d_cart); cudaFree(h->d_sph); cudaFree(h->d_d32);
     cudaFree(h->d_pfeat); cudaFree(h->d_router); cudaFree(h->d_logn);
+    cudaFree(h->d_rlist); cudaFree(h->d_rcount);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
     if (h->cap) cudaStreamDestroy(h->cap);
     for (int b = 0; b < JK_MAX_BRANCHES; ++b) {
@@ -817,6 +832,45 @@ int upload(T **dst, const std::vector<T> &src)
 
 // shell type order: l first, then nprim
 long type_key(const jk_shell &s) { return (long)s.l * 64 + s.nprim; }
+
+// Work items of every launch: per bra, ceil(candidates / chunk) (at least
+// one), where the candidates are the kets (sorted by Q) with Q_ab Q_cd >
+// JK_ITEM_EPS; the last chunk of a bra runs to the molecule's last ket. Also
+// the launch's cost estimate (candidates x modelled FLOPs per quartet).
+int plan_items(jk_handle *h, int chunk)
+{
+    for (auto &L : h->launches) {
+        const PairClass &A = h->classes[L.c1], &B = h->classes[L.c2];
+        std::vector<long long> pre(A.n + 1, 0);
+        double work = 0;
+        for (int m = 0; m < h->nmol; ++m) {
+            const int b0 = A.beg[m], b1 = A.end[m];
+            const int k0 = B.beg[m], k1 = B.end[m];
+            for (int bi = b0; bi < b1; ++bi) {
+                const double qa = h->h_pairs[A.off + bi].Q;
+                const int kfirst = (L.c1 == L.c2) ? bi : k0;
+                // kets with qa * Q_cd > eps form a prefix of [k0, k1)
+                int lo = k0, hi = k1;
+                while (lo < hi) {
+                    int mid = (lo + hi) / 2;
+                    if (qa * h->h_pairs[B.off + mid].Q > JK_ITEM_EPS) lo = mid + 1; else hi = mid;
+                }
+                long long ncand = std::max(0, lo - kfirst);
+                long long nch = std::max(1LL, (ncand + chunk - 1) / chunk);
+                pre[bi + 1] = nch;
+                work += (double)ncand;
+            }
+        }
+        for (int bi = 0; bi < A.n; ++bi) pre[bi + 1] += pre[bi];
+        L.nitems = pre[A.n];
+        cudaFree(L.d_prefix);
+        L.d_prefix = nullptr;
+        if (int rc = upload(&L.d_prefix, pre)) return rc;
+        L.cost = work * class_flops(L.spec[0], 1);
+    }
+    h->chunk = chunk;
+    return JK_OK;
+}
 
 int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells, int32_t nshell,
               const double *coords, int32_t natm, const double *exps, const double *coeffs,
@@ -1180,34 +1234,9 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
                 choose_fragments(s, false);
                 tune_lookup(h->device, s);
             }
-            // work items: per bra, ceil(candidates / JK_CHUNK) (at least one), where the
-            // candidates are the kets (sorted by Q) with Q_ab Q_cd > JK_ITEM_EPS
-            std::vector<long long> pre(A.n + 1, 0);
-            double work = 0;
-            for (int m = 0; m < nmol; ++m) {
-                const int b0 = A.beg[m], b1 = A.end[m];
-                const int k0 = B.beg[m], k1 = B.end[m];
-                for (int bi = b0; bi < b1; ++bi) {
-                    const double qa = h->h_pairs[A.off + bi].Q;
-                    const int kfirst = (i == j) ? bi : k0;
-                    // kets with qa * Q_cd > eps form a prefix of [k0, k1)
-                    int lo = k0, hi = k1;
-                    while (lo < hi) {
-                        int mid = (lo + hi) / 2;
-                        if (qa * h->h_pairs[B.off + mid].Q > JK_ITEM_EPS) lo = mid + 1; else hi = mid;
-                    }
-                    long long ncand = std::max(0, lo - kfirst);
-                    long long nch = std::max(1LL, (ncand + JK_CHUNK - 1) / JK_CHUNK);
-                    pre[bi + 1] = nch;
-                    work += (double)ncand;
-                }
-            }
-            for (int bi = 0; bi < A.n; ++bi) pre[bi + 1] += pre[bi];
-            L.nitems = pre[A.n];
-            if ((rc = upload(&L.d_prefix, pre))) return rc;
-            L.cost = work * class_flops(L.spec[0], 1);
             h->launches.push_back(L);
         }
+    if ((rc = plan_items(h.get(), JK_CHUNK))) return rc;
     std::stable_sort(h->launches.begin(), h->launches.end(), [](const Launch &x, const Launch &y) { return x.cost > y.cost; });
 
     // ---- per-build scratch
@@ -1231,7 +1260,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
     CK(cudaMalloc(&h->d_dmax32, sizeof(float) * dtot));
     CK(cudaMalloc(&h->d_dmax_mol, sizeof(unsigned long long) * nmol));
     CK(cudaMalloc(&h->d_mols, sizeof(JkMol) * nmol));
-    const size_t nl = h->launches.size() * 2;
+    const size_t nl = h->launches.size() * 3;   // FP64, FP32 and the routed list kernel
     CK(cudaMalloc(&h->d_work, sizeof(unsigned long long) * nl));
     CK(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 3 * nl));
     CK(cudaMalloc(&h->d_err, sizeof(int)));
@@ -1329,14 +1358,18 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
     // kernels for this combination
     std::vector<KSpec> specs;
     std::vector<int> lidx, tier;
+    // tier 0 FP64, 1 FP32; routed builds add tier 2, the FP32 list kernel
+    // of the quartets the router released from the FP64 tier (the router
+    // itself runs in the FP64 tier only)
+    const bool routed = mode == JK_PREC_MIXED_ROUTED;
     for (size_t i = 0; i < h->launches.size(); ++i) {
-        for (int t = 0; t < 2; ++t) {
-            const bool two = mode == JK_PREC_MIXED || mode == JK_PREC_MIXED_ROUTED;
-            bool use = (t == 0) ? (mode == JK_PREC_FP64 || two) : (mode == JK_PREC_FP32 || two);
+        for (int t = 0; t < 3; ++t) {
+            const bool two = mode == JK_PREC_MIXED || routed;
+            bool use = (t == 0) ? (mode == JK_PREC_FP64 || two) : (t == 1 ? (mode == JK_PREC_FP32 || two) : routed);
             if (!use) continue;
-            KSpec s = h->launches[i].spec[t];
+            KSpec s = h->launches[i].spec[t == 0 ? 0 : 1];
             s.ndm = ndm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0;
-            s.mode = logs ? 2 : (mode == JK_PREC_MIXED_ROUTED ? 1 : 0);
+            s.mode = logs ? 2 : (routed ? (t == 0 ? 1 : (t == 2 ? 3 : 0)) : 0);
             s.op = h->omega == 0.0 ? 0 : (h->omega > 0.0 ? 1 : 2);
             specs.push_back(s);
             lidx.push_back((int)i);
@@ -1373,6 +1406,27 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         for (int m = 0; m < h->nmol; ++m) { h->d32_off[m] = tot; tot += (size_t)ndm * h->nao_cart[m] * h->nao_cart[m]; }
         CK(cudaMalloc(&h->d_d32, sizeof(float) * std::max<size_t>(tot, 1)));
         h->d32_ndm = ndm;
+        ++h->cart_gen;
+    }
+    // routed builds: one list per class pair for the quartets the router
+    // releases from the FP64 tier, sized by the pair's share of the estimated
+    // work (at least 4,096 entries); a quartet that finds its list full stays
+    // in FP64
+    if (routed && !h->d_rlist) {
+        CK(cudaStreamSynchronize(st));
+        double tc2 = 0;
+        for (auto &L : h->launches) tc2 += L.cost;
+        h->rl_off.assign(h->launches.size(), 0);
+        h->rl_cap.assign(h->launches.size(), 0);
+        long long tot = 0;
+        for (size_t i = 0; i < h->launches.size(); ++i) {
+            const double share = tc2 > 0 ? h->launches[i].cost / tc2 : 1.0 / h->launches.size();
+            h->rl_cap[i] = std::max(4096LL, (long long)(h->route_cap * share));
+            h->rl_off[i] = tot;
+            tot += h->rl_cap[i];
+        }
+        CK(cudaMalloc(&h->d_rlist, sizeof(JkRouted) * (size_t)std::max(tot, 1LL)));
+        CK(cudaMalloc(&h->d_rcount, sizeof(unsigned long long) * std::max<size_t>(h->launches.size(), 1)));
         ++h->cart_gen;
     }
     // per-molecule descriptors
@@ -1420,7 +1474,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         max_nsh = std::max(max_nsh, h->mol_sh0[m + 1] - h->mol_sh0[m]);
         max_nao = std::max(max_nao, h->nao_cart[m]);
     }
-    const size_t nl = h->launches.size() * 2;
+    const size_t nl = h->launches.size() * 3;   // counters per launch and tier (incl. the routed list tier)
     const double inf = INFINITY;
     const bool prof = h->profile && stats;
     if (prof && h->prof_ev.size() < 2 * specs.size()) {
@@ -1455,6 +1509,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         CK(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long) * nl, s0));
         CK(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 3 * nl, s0));
         CK(cudaMemsetAsync(h->d_dmax_mol, 0, sizeof(unsigned long long) * h->nmol, s0));
+        if (routed) CK(cudaMemsetAsync(h->d_rcount, 0, sizeof(unsigned long long) * h->launches.size(), s0));
         jk_dmax_kernel<<<h->nshell, 128, 0, s0>>>(h->d_mols, h->d_sh_mol, h->d_mol_sh0, h->d_sh_ao, h->d_sh_nc, ndm,
                                                   h->d_dmax, h->d_dmax32, h->d_dmax_mol, h->d_err);
         CK(cudaGetLastError());
@@ -1471,7 +1526,10 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             for (int b = 1; b < nbranch; ++b) CK(cudaStreamWaitEvent(h->side[b - 1], h->ev_fork, 0));
         }
         for (size_t k = 0; k < specs.size(); ++k) {
-            cudaStream_t sk = (nbranch > 1 && k % nbranch) ? h->side[k % nbranch - 1] : s0;
+            // a routed class pair keeps its three launches on one stream (the
+            // list kernel reads what the FP64 launch wrote)
+            const size_t br = routed ? (size_t)lidx[k] : k;
+            cudaStream_t sk = (nbranch > 1 && br % nbranch) ? h->side[br % nbranch - 1] : s0;
             const Launch &L = h->launches[lidx[k]];
             const PairClass &A = h->classes[L.c1], &B = h->classes[L.c2];
             JkClassArgs a;
@@ -1488,7 +1546,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.dmax_mol = reinterpret_cast<const double *>(h->d_dmax_mol);
             a.rys64 = h->d_rys64;
             a.rys32 = h->d_rys32;
-            const int slot = lidx[k] * 2 + tier[k];
+            const int slot = lidx[k] * 3 + tier[k];
             a.work = h->d_work + slot;
             a.stats = h->d_stats + 3 * slot;
             a.err = h->d_err;
@@ -1498,8 +1556,10 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                 if (tier[k] == 0) { a.lo = tau; a.hi = inf; }
                 else { a.lo = cutoff; a.hi = tau; }
             } else if (mode == JK_PREC_MIXED_ROUTED) {
+                // the FP32 tier keeps the Schwarz split; the band goes to the
+                // FP64 tier, which routes it (tier 2 reads its list)
                 if (tier[k] == 0) { a.lo = tau; a.hi = inf; }
-                else { a.lo = cutoff; a.hi = band_hi; }
+                else { a.lo = cutoff; a.hi = tau; }
             } else {
                 a.lo = cutoff; a.hi = inf;
             }
@@ -1511,12 +1571,16 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             // FP32 screening unless the cutoff is below the FP32 range; one
             // choice for every launch of the build, so that the tiers of a
             // mixed build compare the same bounds in the same precision
-            a.scr32 = cutoff >= 1e-30 ? 1 : 0;
+            a.scr32 = (cutoff >= 1e-30 && !h->screen64) ? 1 : 0;
             a.lo32 = (float)a.lo;
             a.hi32 = std::isinf(a.hi) ? INFINITY : (float)a.hi;
             a.tau32 = (float)tau;
             a.band_hi32 = (float)band_hi;
-            a.tier = tier[k];
+            a.tier = tier[k] == 0 ? 0 : 1;
+            a.rlist = routed ? h->d_rlist + h->rl_off[lidx[k]] : nullptr;
+            a.rcount = routed ? h->d_rcount + lidx[k] : nullptr;
+            a.rcap = routed ? h->rl_cap[lidx[k]] : 0;
+            a.asym64 = h->asym64;
             a.log_x = logs ? logs->x : nullptr;
             a.log_y = logs ? logs->y : nullptr;
             a.log_n = h->d_logn;
@@ -1526,7 +1590,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             const long long nunits = L.nitems * specs[k].gx;   // work items x slabs
             a.item_lo = nunits * h->part_index / h->part_count;
             a.item_hi = nunits * (h->part_index + 1) / h->part_count;
-            a.chunk = JK_CHUNK;
+            a.chunk = h->chunk;
             a.prim_eps = std::min(cutoff, h->prim_eps);
             a.prim_eps32 = (float)a.prim_eps;
             a.omega = std::fabs(h->omega);
@@ -1575,9 +1639,9 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         // stream and replayed on the caller's; per-call pointers live in the
         // device descriptors copied above, so the graph stays valid.
         char keyb[160];
-        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d/%d/%d/%a", ndm, with_j, with_k, mode, cutoff,
-                 h->tau32, h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0, h->part_index,
-                 h->part_count, h->prim_eps);
+        snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d/%d/%d/%a/%d/%d", ndm, with_j, with_k, mode,
+                 cutoff, h->tau32, h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0, h->part_index,
+                 h->part_count, h->prim_eps, h->asym64, h->screen64);
         std::string key = keyb;
         char ob[40];
         snprintf(ob, sizeof ob, "/%a", h->omega);
@@ -1617,11 +1681,11 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         stats->kernel_launches = (int64_t)specs.size() + nlaunch_aux;
         if (prof) { h->prof.clear(); h->prof_slot.clear(); }
         for (size_t k = 0; k < specs.size(); ++k) {
-            const int slot = lidx[k] * 2 + tier[k];
+            const int slot = lidx[k] * 3 + tier[k];
             unsigned long long nq = cnt[3 * slot], np = cnt[3 * slot + 1];
             if (tier[k] == 0) stats->quartets_fp64 += (int64_t)nq;
             else stats->quartets_fp32 += (int64_t)nq;
-            if (tier[k] == 1 && mode == JK_PREC_MIXED_ROUTED) routed_fp32 += (int64_t)cnt[3 * slot + 2];
+            if (tier[k] == 2) routed_fp32 += (int64_t)nq;
             stats->prim_quartets += (int64_t)np;
             stats->flops_model += flops_of(specs[k], ndm, nq, np);
             if (prof) {
@@ -1629,7 +1693,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
                 const KSpec &x = specs[k];
                 p.la = x.la; p.lb = x.lb; p.lc = x.lc; p.ld = x.ld;
                 p.na = x.na; p.nb = x.nb; p.nc = x.nc; p.nd = x.nd;
-                p.tier = tier[k];
+                p.tier = tier[k] == 0 ? 0 : 1;
                 p.threads_per_quartet = x.G();
                 p.regs = ki[k].regs;
                 p.local_bytes = ki[k].local_bytes;
@@ -1794,7 +1858,7 @@ int tune_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int
         for (auto &it : items)
             for (auto c : it.c) {
                 c.ndm = ndm; c.doj = with_j ? 1 : 0; c.dok = with_k ? 1 : 0;
-                c.mode = mode == JK_PREC_MIXED_ROUTED ? 1 : 0;
+                c.mode = (mode == JK_PREC_MIXED_ROUTED && it.t == 0) ? 1 : 0;
                 c.op = h->omega == 0.0 ? 0 : (h->omega > 0.0 ? 1 : 2);
                 all.push_back(c);
             }
@@ -1812,7 +1876,7 @@ int tune_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int
     size_t nround = 0;
     for (auto &it : items) nround = std::max(nround, it.c.size());
     std::map<int, int> by_slot;
-    for (size_t i = 0; i < items.size(); ++i) by_slot[items[i].l * 2 + items[i].t] = (int)i;
+    for (size_t i = 0; i < items.size(); ++i) by_slot[items[i].l * 3 + items[i].t] = (int)i;
     const int o_prof = h->profile, o_branches = h->branches, o_graph = h->use_graph;
     h->profile = 1;
     h->branches = 1;
@@ -1980,6 +2044,28 @@ int jk_set_option(jk_handle *h, const char *key, double value)
         if (!(value >= 1 && value <= JK_MAX_BRANCHES + 1)) return fail(JK_ERR_ARG, "branches must be in [1, %d]", JK_MAX_BRANCHES + 1);
         h->branches = (int)value;
     }
+    else if (k == "asym64") h->asym64 = value != 0;
+    else if (k == "chunk") {
+        if (!(value >= 32 && value <= 4096)) return fail(JK_ERR_ARG, "chunk must be in [32, 4096]");
+        if ((int)value != h->chunk) {
+            cudaDeviceSynchronize();
+            for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
+            h->graphs.clear();
+            if (int rc = plan_items(h, (int)value)) return rc;
+        }
+    }
+    else if (k == "screen64") h->screen64 = value != 0;
+    else if (k == "route_cap") {
+        if (!(value >= 1 && value <= 1e9)) return fail(JK_ERR_ARG, "route_cap must be in [1, 1e9]");
+        if (value != h->route_cap) {
+            cudaDeviceSynchronize();
+            cudaFree(h->d_rlist); cudaFree(h->d_rcount);
+            h->d_rlist = nullptr; h->d_rcount = nullptr;
+            for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
+            h->graphs.clear();
+        }
+        h->route_cap = value;
+    }
     else return fail(JK_ERR_ARG, "unknown option '%s'", key);
     return JK_OK;
 }
@@ -1999,6 +2085,10 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "prim_eps") *value = h->prim_eps;
     else if (k == "omega") *value = h->omega;
     else if (k == "part_index") *value = h->part_index;
+    else if (k == "asym64") *value = h->asym64;
+    else if (k == "chunk") *value = h->chunk;
+    else if (k == "screen64") *value = h->screen64;
+    else if (k == "route_cap") *value = h->route_cap;
     else if (k == "graphs") *value = (double)h->graphs.size();
     else if (k == "init_ms") *value = h->init_ms;
     else if (k == "compile_ms") *value = h->compile_ms;
@@ -2289,7 +2379,7 @@ int jk_compile_class(int32_t la, int32_t lb, int32_t lc, int32_t ld, int32_t na,
         nd > JK_NPRIM_MAX)
         return fail(JK_ERR_UNSUPPORTED, "primitive count out of range");
     if (n_dm < 1 || n_dm > JK_NDM_MAX || (!with_j && !with_k)) return fail(JK_ERR_ARG, "bad n_dm or flags");
-    if (mode < 0 || mode > 2 || (mode == 2 && fp32)) return fail(JK_ERR_ARG, "bad mode");
+    if (mode < 0 || mode > 3 || (mode == 2 && fp32) || (mode == 3 && !fp32)) return fail(JK_ERR_ARG, "bad mode");
     if (op < 0 || op > 2) return fail(JK_ERR_ARG, "bad op");
     KSpec s;
     s.kind = 0;
@@ -2311,7 +2401,7 @@ int jk_compile_basis(const jk_shell *shells, int32_t nshell, int32_t n_dm, int32
 {
     if (!shells || nshell < 1) return fail(JK_ERR_ARG, "no shells");
     if (n_dm < 1 || n_dm > JK_NDM_MAX || (!with_j && !with_k)) return fail(JK_ERR_ARG, "bad n_dm or flags");
-    if (mode < 0 || mode > 2 || (mode == 2 && fp32)) return fail(JK_ERR_ARG, "bad mode");
+    if (mode < 0 || mode > 3 || (mode == 2 && fp32) || (mode == 3 && !fp32)) return fail(JK_ERR_ARG, "bad mode");
     // shell types (l, nprim) -> pair classes (larger type first) -> class pairs
     std::vector<std::pair<int, int>> types;
     for (int i = 0; i < nshell; ++i) {

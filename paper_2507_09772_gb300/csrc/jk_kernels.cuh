@@ -57,7 +57,7 @@ __device__ __forceinline__ float jk_rsqrt(float x) { return rsqrtf(x); }
 // u = x^2 / T, w = w_h / sqrt(T) holds (evaluated in the tier's precision).
 template <int N>
 __device__ __forceinline__ void jk_rys_one(double T, int r, const double *__restrict__ tab,
-                                           double &u, double &w)
+                                           double &u, double &w, int /*a64*/)
 {
     if (T >= rys64_tmax[N]) {
         double s = rsqrt(T);
@@ -85,11 +85,23 @@ __device__ __forceinline__ void jk_rys_one(double T, int r, const double *__rest
     w = aw;
 }
 
+// FP32: `tab` is this N's table alone, as the class kernel stages it in
+// shared memory: per interval the 16 N coefficients (per root the eight of u,
+// then per root the eight of w) and four floats of padding, so that the
+// 16-byte vectors of different intervals fall in different bank groups.
 template <int N>
 __device__ __forceinline__ void jk_rys_one(float T, int r, const float *__restrict__ tab,
-                                           float &u, float &w)
+                                           float &u, float &w, int a64)
 {
+    static_assert(RYS32_DEG == 7, "two float4 per function");
     if (T >= (float)rys32_tmax[N]) {
+        if (a64) {
+            // the same limit evaluated in FP64, rounded once to FP32
+            const double s = rsqrt((double)T);
+            u = (float)(rys_gh[rys_gh_offset[N - 1] + r] * (s * s));
+            w = (float)(rys_gh[rys_gh_offset[N - 1] + N + r] * s);
+            return;
+        }
         // u = x^2 / T, w = w_h / sqrt(T): no cancellation, so FP32 keeps
         // ~2 ulp; the Gauss-Hermite constants themselves are FP64-derived
         const float s = rsqrtf(T);
@@ -97,19 +109,25 @@ __device__ __forceinline__ void jk_rys_one(float T, int r, const float *__restri
         w = (float)rys_gh[rys_gh_offset[N - 1] + N + r] * s;
         return;
     }
-    int k = min((int)(T * (float)RYS32_INVH), rys32_nint[N] - 1);
+    int k = min((int)(T * (float)RYS32_INVH), rys32_nint_c[N] - 1);
     float x = (T - k * (float)RYS32_H) * (float)(2.0 * RYS32_INVH) - 1.0f;
-    const float *cu = tab + rys32_offset[N] + k * (2 * N * (RYS32_DEG + 1)) + r * (RYS32_DEG + 1);
-    const float *cw = cu + N * (RYS32_DEG + 1);
-    float au = __ldg(cu + RYS32_DEG), aw = __ldg(cw + RYS32_DEG);
-#pragma unroll
-    for (int i = RYS32_DEG - 1; i >= 0; --i) {
-        au = fmaf(au, x, __ldg(cu + i));
-        aw = fmaf(aw, x, __ldg(cw + i));
-    }
+    const float4 *cu = reinterpret_cast<const float4 *>(tab + k * (16 * N + 4) + r * 8);
+    const float4 *cw = cu + N * 2;
+    const float4 u0 = cu[0], u1 = cu[1], w0 = cw[0], w1 = cw[1];
+    float au = fmaf(fmaf(fmaf(u1.w, x, u1.z), x, u1.y), x, u1.x);
+    float aw = fmaf(fmaf(fmaf(w1.w, x, w1.z), x, w1.y), x, w1.x);
+    au = fmaf(fmaf(fmaf(fmaf(au, x, u0.w), x, u0.z), x, u0.y), x, u0.x);
+    aw = fmaf(fmaf(fmaf(fmaf(aw, x, w0.w), x, w0.z), x, w0.y), x, w0.x);
     u = au;
     w = aw;
 }
+
+template <typename R> struct JkIsFloat { static constexpr bool v = false; };
+template <> struct JkIsFloat<float> { static constexpr bool v = true; };
+
+// Floats of the FP32 Rys table of the N-root rule in its shared-memory
+// layout (intervals padded from 16 N to 16 N + 4 floats).
+template <int N> struct JkRysTab32 { static constexpr int n = rys32_nint_c[N] * (16 * N + 4); };
 
 // --------------------------------------------------------- 2D integrals
 // One direction, one root: vertical recurrence on (n on A, m on C) up to
@@ -256,12 +274,12 @@ __device__ __forceinline__ void jk_group_sync(unsigned gmask)
 // Root r (< NRE) of the operator: set 0 at T (1/r) or at theta T (erf);
 // for OP 2 set 1 is the erf part with negated weight. Returns u and w * pref.
 template <int NR, int OP, typename R>
-__device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, int r, const R *__restrict__ rys,
-                                           R &u, R &wp)
+__device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, int a64, int r,
+                                           const R *__restrict__ rys, R &u, R &wp)
 {
     R uu, ww;
     if (OP == 0 || (OP == 2 && r < NR)) {
-        jk_rys_one<NR>(Tt, r, rys, uu, ww);
+        jk_rys_one<NR>(Tt, r, rys, uu, ww, a64);
         u = uu;
         wp = ww * pref;
     } else {
@@ -269,7 +287,7 @@ __device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, in
         const R om = (R)omega;
         const R rd = jk_rsqrt(om * om + rho);
         const R st = om * rd, th = st * st;
-        jk_rys_one<NR>(th * Tt, OP == 2 ? r - NR : r, rys, uu, ww);
+        jk_rys_one<NR>(th * Tt, OP == 2 ? r - NR : r, rys, uu, ww, a64);
         u = th * uu;
         wp = (OP == 2 ? -st : st) * ww * pref;
     }
@@ -278,7 +296,7 @@ __device__ __forceinline__ void jk_op_root(R Tt, R rho, R pref, double omega, in
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
           int GA, int GB, int GC, int GD, typename R, int OP = 0,
           int NT = JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>::G>
-__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, float qthr, double omega,
+__device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, float qthr, double omega, int a64,
                                            const typename JkPP<R>::T *__restrict__ pp,
                                            const R *__restrict__ rys, R *grp, unsigned gmask, int tg, bool act,
                                            const JkOffsets<JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP>> &off,
@@ -295,18 +313,20 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
     // primitive pairs are sorted by their Schwarz factor q (largest first):
     // stop a loop at the first q_ij q_kl <= qthr (= prim_eps / Dmax), compared
     // in FP32 (a product below the FP32 range is below any threshold that
-    // matters; qthr < 0 screens nothing)
+    // matters; qthr < 0 screens nothing). The ket's primitive pairs (one
+    // record per lane and kl) are the outer loop, so each is loaded once; the
+    // bra's (the same for the whole group or warp) the inner one.
     const float qthf = qthr;
-    const float qk0 = jk_pp_q(kpp[0]);
+    const float qb0 = jk_pp_q(bpp[0]);
     int nprim = 0;
 #pragma unroll 1
-    for (int ij = 0; ij < NPA * NPB; ++ij) {
-        const PPT bp = bpp[ij];
-        const float qb = jk_pp_q(bp);
-        if (qb * qk0 <= qthf) break;
-        for (int kl = 0; kl < NPC * NPD; ++kl) {
-            const PPT kp = kpp[kl];
-            if (qb * jk_pp_q(kp) <= qthf) break;
+    for (int kl = 0; kl < NPC * NPD; ++kl) {
+        const PPT kp = kpp[kl];
+        const float qk = jk_pp_q(kp);
+        if (qb0 * qk <= qthf) break;
+        for (int ij = 0; ij < NPA * NPB; ++ij) {
+            const PPT bp = bpp[ij];
+            if (jk_pp_q(bp) * qk <= qthf) break;
             ++nprim;
             const R p = bp.p, q = kp.p;
             const R rpq = jk_rsqrt(p + q);
@@ -320,7 +340,7 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
 #pragma unroll
                 for (int r = 0; r < NRE; ++r) {
                     R u, wp;
-                    jk_op_root<NR, OP, R>(Tt, rho, pref, omega, r, rys, u, wp);
+                    jk_op_root<NR, OP, R>(Tt, rho, pref, omega, a64, r, rys, u, wp);
                     const R b00 = (R)0.5 * u * inv_pq;
                     const R b10 = bp.inv2p * ((R)1 - u * qf);
                     const R b01 = kp.inv2p * ((R)1 - u * pf);
@@ -351,7 +371,7 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
                 R *roots = grp + NRE * 3 * S::NI;   // [0, NRE): u ; [NRE, 2 NRE): w * pref
                 for (int r = tg; r < NRE && tg < NT; r += NT) {
                     R u, wp;
-                    jk_op_root<NR, OP, R>(Tt, rho, pref, omega, r, rys, u, wp);
+                    jk_op_root<NR, OP, R>(Tt, rho, pref, omega, a64, r, rys, u, wp);
                     roots[r] = u;
                     roots[NRE + r] = wp;
                 }
@@ -406,6 +426,31 @@ template <typename R> __device__ __forceinline__ const R *jk_rys(const JkClassAr
 template <> __device__ __forceinline__ const double *jk_rys<double>(const JkClassArgs &a) { return a.rys64; }
 template <> __device__ __forceinline__ const float *jk_rys<float>(const JkClassArgs &a) { return a.rys32; }
 
+// ---------------------------------------------- routed builds: the FP64 tier
+// The FP64 tier of a routed build is the only tier that runs the router: the
+// lanes in `rel` (band quartets the router releases) append (bra item, ket j,
+// density factor) to the launch's list while it has room, for the FP32 list
+// kernel (MODE 3) of the class pair. Returns whether this lane's quartet was
+// listed; a quartet that finds the list full stays in FP64. All 32 lanes of
+// the warp call it.
+__device__ __forceinline__ bool jk_route_out(const JkClassArgs &args, bool rel, int item, int j, float dq)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, rel);
+    if (!m) return false;
+    const int lane = threadIdx.x & 31, first = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == first) base = atomicAdd(args.rcount, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, first);
+    const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
+    const bool listed = rel && pos < args.rcap;
+    if (listed) {
+        JkRouted e;
+        e.item = item; e.ket = j; e.dmq = dq; e.pad = 0;
+        args.rlist[pos] = e;
+    }
+    return listed;
+}
+
 // ------------------------------------------------- screening of a candidate
 template <int MODE>
 __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
@@ -416,7 +461,7 @@ __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const J
 // one, kets being sorted by Q) above lo.
 template <int MODE>
 __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkPairFeat &braf,
-                                          const JkMol &mol, const double *dmx, double dmol, int j, int ke,
+                                          const JkMol &mol, const double *dmx, double dmol, int item, int j, int ke,
                                           bool &sig, bool &stop, bool &band, float &dmq, unsigned short *rsm)
 {
     sig = false;
@@ -426,14 +471,17 @@ __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair 
     float B = 0.0f;
     jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, j, ke, sig, stop, band, dmq, B);
     if (MODE == 1) {
-        // learned router for the band candidates, all lanes together on the tensor cores
+        // learned router for the band candidates, all lanes together on the
+        // tensor cores; `band` then marks the quartets released to FP32
+        bool listed = false;
         if (__ballot_sync(0xffffffffu, band)) {
             const JkPairFeat kf = band ? args.ket_feat[j] : braf;
             const bool to32 = jk_router_to_fp32_warp(args.router, braf, kf, band ? B : 2.0f * args.tau32,
                                                      band ? dmq : 1.0f, args.tau32, rsm);
-            if (band) sig = (args.tier == 1) ? to32 : !to32;
+            listed = jk_route_out(args, band && to32, item, j, dmq);
+            if (band) sig = !listed;
         }
-        band = band && sig;
+        band = listed;
     }
 }
 
@@ -685,10 +733,26 @@ jk_class_kernel(const JkClassArgs args)
     typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP> S;
     constexpr int G = S::G;
     constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
-    extern __shared__ double jk_smem_raw[];
+    extern __shared__ __align__(16) double jk_smem_raw[];
     const int lane = threadIdx.x & 31;
     const typename JkPP<R>::T *pp = jk_pp<R>(args);
     const R *rys = jk_rys<R>(args);
+    // The FP32 tier reads its Rys table from shared memory: lanes gather
+    // coefficients of unrelated intervals, which from global memory costs one
+    // L1 wavefront per lane and load. Only this class's N-root table, copied
+    // once per (persistent) CTA, ahead of the groups' 2D tables.
+    R *smem_groups = reinterpret_cast<R *>(jk_smem_raw);
+    if constexpr (JkIsFloat<R>::v) {
+        constexpr int NT = JkRysTab32<S::NR>::n, V = 4 * S::NR;   // float4 per interval (unpadded)
+        static_assert(NT % 4 == 0, "whole float4 vectors");
+        float4 *dst = reinterpret_cast<float4 *>(jk_smem_raw);
+        const float4 *src = reinterpret_cast<const float4 *>(args.rys32 + rys32_offset[S::NR]);
+        for (int i = threadIdx.x; i < rys32_nint_c[S::NR] * V; i += blockDim.x)
+            dst[(i / V) * (V + 1) + i % V] = __ldg(src + i);
+        __syncthreads();
+        rys = reinterpret_cast<const R *>(jk_smem_raw);
+        smem_groups = reinterpret_cast<R *>(jk_smem_raw) + NT;
+    }
 
     static_assert(X == 1 || (G > 32 && G % X == 0), "a split group spans whole CTAs");
     if constexpr (G <= 32) {
@@ -697,7 +761,7 @@ jk_class_kernel(const JkClassArgs args)
         const int gw = lane / G, tg = lane - gw * G;
         const bool active = gw < NGW;
         const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((active ? gw : 0) * G));
-        R *grp = reinterpret_cast<R *>(jk_smem_raw) + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
+        R *grp = smem_groups + (size_t)(wib * NGW + (active ? gw : 0)) * S::SMEM_GROUP;
         // router scratch, 1 KB per warp (MODE 1)
         __shared__ __align__(16) unsigned short s_rsm[MODE == 1 ? 4 * 32 * JK_RT_NINP : 2];
         // ket queue per warp: at most NGW - 1 + 32 entries; band queue (MODE 1):
@@ -710,6 +774,57 @@ jk_class_kernel(const JkClassArgs args)
         const int gd = tg % GD, gc = (tg / GD) % GC, gb = (tg / (GD * GC)) % GB, ga = tg / (GD * GC * GB);
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
+        if constexpr (MODE == 3) {
+            // FP32 list kernel of a routed build: the band quartets the FP64
+            // tier released, one per group; each bra's J block is flushed on
+            // its own (the quartets of a warp belong to unrelated bras)
+            const long long n = min((long long)*args.rcount, args.rcap);
+            unsigned long long nq = 0, nprim = 0;
+            for (;;) {
+                long long t = 0;
+                if (lane == 0) t = (long long)atomicAdd(args.work, (unsigned long long)NGW);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if (t >= n) break;
+                const long long e = t + gw;
+                if (active && e < n) {
+                    const JkRouted rq = args.rlist[e];
+                    const JkPair bra = args.bra[rq.item];
+                    const JkPair ket = args.ket[rq.ket];
+                    const JkMol mol = args.mols[bra.mol];
+                    R T[S::EPT];
+#pragma unroll
+                    for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
+                    const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP>(
+                        bra, ket, __fdiv_rn(args.prim_eps32, rq.dmq), args.omega, args.asym64, pp, rys, grp, gmask,
+                        tg, true, off, T);
+                    R f = (R)1;
+                    if (bra.a == bra.b) f *= (R)0.5;
+                    if (ket.a == ket.b) f *= (R)0.5;
+                    if (args.same_class && rq.ket == rq.item) f *= (R)0.5;
+                    R jab[NDM][FA][FB];
+#pragma unroll
+                    for (int m = 0; m < NDM; ++m)
+#pragma unroll
+                        for (int i = 0; i < FA; ++i)
+#pragma unroll
+                            for (int jj = 0; jj < FB; ++jj) jab[m][i][jj] = (R)0;
+                    const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+                    jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
+                                                                 ket.b_ao + gd * FD, jab);
+                    if (DOJ) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+                    if (tg == 0) { ++nq; nprim += np; }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                nq += __shfl_xor_sync(0xffffffffu, nq, o);
+                nprim += __shfl_xor_sync(0xffffffffu, nprim, o);
+            }
+            if (lane == 0 && nq) {
+                atomicAdd(args.stats, nq);
+                atomicAdd(args.stats + 1, nprim);
+            }
+            return;
+        }
         for (;;) {
             long long t = 0;
             if (lane == 0) t = args.item_lo + (long long)atomicAdd(args.work, 1ull);
@@ -782,10 +897,13 @@ jk_class_kernel(const JkClassArgs args)
                         const float bj = mine ? s_bb[wib][lane] : 2.0f * args.tau32;
                         const JkPairFeat kf = mine ? args.ket_feat[j] : braf;
                         const bool to32 = jk_router_to_fp32_warp(args.router, braf, kf, bj, dj, args.tau32, rsm);
-                        const bool keep = mine && ((args.tier == 1) ? to32 : !to32);
+                        // released quartets go to the FP32 list kernel; the
+                        // rest of the band stays here, in FP64
+                        const bool listed = jk_route_out(args, mine && to32, item, j, dj);
+                        const bool keep = mine && !listed;
                         const unsigned mk = __ballot_sync(0xffffffffu, keep);
                         nq += __popc(mk);
-                        nband += __popc(mk);
+                        nband += __popc(__ballot_sync(0xffffffffu, listed));
                         if (keep) {
                             const int pos = qn + __popc(mk & lt);
                             s_qk[wib][pos] = j;
@@ -818,7 +936,8 @@ jk_class_kernel(const JkClassArgs args)
 #pragma unroll
                         for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
                         const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP>(
-                            bra, ket, __fdiv_rn(args.prim_eps32, dmk), args.omega, pp, rys, grp, gmask, tg, true,
+                            bra, ket, __fdiv_rn(args.prim_eps32, dmk), args.omega, args.asym64, pp, rys, grp, gmask,
+                            tg, true,
                             off, T);
                         if (tg == 0) nprim += np;
                         R f = (R)1;
@@ -870,9 +989,64 @@ jk_class_kernel(const JkClassArgs args)
         const bool act = tg < NTC;
         const int tgc = act ? tg : 0;
         int gd = tgc % GD, gc = (tgc / GD) % GC, gb = (tgc / (GD * GC)) % GB, ga = tgc / (GD * GC * GB);
-        R *grp = reinterpret_cast<R *>(jk_smem_raw);
+        R *grp = smem_groups;
         JkOffsets<S> off;
         jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
+        if constexpr (MODE == 3) {
+            // FP32 list kernel of a routed build: one released quartet (or one
+            // of its X slabs) per CTA at a time
+            const long long n = min((long long)*args.rcount, args.rcap);
+            unsigned long long nq = 0, nprim = 0;
+            for (;;) {
+                if (threadIdx.x == 0) s_item = (long long)atomicAdd(args.work, 1ull);
+                __syncthreads();
+                const long long tt = s_item;
+                __syncthreads();
+                if (tt >= n * X) break;
+                const long long e = X == 1 ? tt : tt / X;
+                const int slab = (int)(tt - e * X);
+                if constexpr (X > 1) {
+                    const int tgl = slab * NTC + tgc;
+                    gd = tgl % GD; gc = (tgl / GD) % GC; gb = (tgl / (GD * GC)) % GB; ga = tgl / (GD * GC * GB);
+                    jk_make_offsets<LA, LB, LC, LD, GA, GB, GC, GD, S>(ga, gb, gc, gd, off);
+                }
+                const JkRouted rq = args.rlist[e];
+                const JkPair bra = args.bra[rq.item];
+                const JkPair ket = args.ket[rq.ket];
+                const JkMol mol = args.mols[bra.mol];
+                R T[S::EPT];
+#pragma unroll
+                for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
+                const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP, NTC>(
+                    bra, ket, __fdiv_rn(args.prim_eps32, rq.dmq), args.omega, args.asym64, pp, rys, grp, 0u, tg, act,
+                    off, T);
+                if (act) {
+                    R f = (R)1;
+                    if (bra.a == bra.b) f *= (R)0.5;
+                    if (ket.a == ket.b) f *= (R)0.5;
+                    if (args.same_class && rq.ket == rq.item) f *= (R)0.5;
+                    R jab[NDM][FA][FB];
+#pragma unroll
+                    for (int m = 0; m < NDM; ++m)
+#pragma unroll
+                        for (int i = 0; i < FA; ++i)
+#pragma unroll
+                            for (int jj = 0; jj < FB; ++jj) jab[m][i][jj] = (R)0;
+                    const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
+                    jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
+                                                                 ket.b_ao + gd * FD, jab);
+                    if (DOJ) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+                }
+                if (slab == 0) { ++nq; nprim += np; }
+                // every thread is done with this entry's shared tables
+                __syncthreads();
+            }
+            if (threadIdx.x == 0 && nq) {
+                atomicAdd(args.stats, nq);
+                atomicAdd(args.stats + 1, nprim);
+            }
+            return;
+        }
         for (;;) {
             if (threadIdx.x == 0) s_item = args.item_lo + (long long)atomicAdd(args.work, 1ull);
             __syncthreads();
@@ -913,7 +1087,8 @@ jk_class_kernel(const JkClassArgs args)
                 if (threadIdx.x < 32) {
                     bool sig, stop, band;
                     float dmq;
-                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, s_rsm);
+                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, item, base + lane, ke, sig, stop, band, dmq,
+                                    s_rsm);
                     s_dm[lane] = dmq;
                     const unsigned msk = __ballot_sync(0xffffffffu, sig);
                     const int anystop = __any_sync(0xffffffffu, stop);
@@ -933,7 +1108,8 @@ jk_class_kernel(const JkClassArgs args)
 #pragma unroll
                     for (int k = 0; k < S::EPT; ++k) T[k] = (R)0;
                     const int np = jk_quartet<LA, LB, LC, LD, NPA, NPB, NPC, NPD, GA, GB, GC, GD, R, OP, NTC>(
-                        bra, ket, __fdiv_rn(args.prim_eps32, s_dm[myket - base]), args.omega, pp, rys, grp, 0u, tg,
+                        bra, ket, __fdiv_rn(args.prim_eps32, s_dm[myket - base]), args.omega, args.asym64, pp, rys,
+                        grp, 0u, tg,
                         act, off, T);
                     nprim += np;
                     if (act) {
@@ -994,7 +1170,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
     static_assert(X == 1 || (S::G > 32 && S::G % X == 0), "a split group spans whole CTAs");
     constexpr int G = S::G;
     constexpr int FA = S::FA, FB = S::FB, FC = S::FC, FD = S::FD;
-    extern __shared__ double jk_smem_raw[];
+    extern __shared__ __align__(16) double jk_smem_raw[];
     const int lane = threadIdx.x & 31;
     if constexpr (G <= 32) {
         constexpr int NGW = 32 / G;
@@ -1017,7 +1193,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
                 double T[S::EPT];
 #pragma unroll
                 for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
-                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0f, 0.0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
+                jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double>(pr, pr, -1.0f, 0.0, 0, args.pp64, args.rys64, grp, gmask, tg, true, off, T);
                 if (ga == gc && gb == gd) {
 #pragma unroll
                     for (int ia = 0; ia < FA; ++ia)
@@ -1053,7 +1229,7 @@ jk_schwarz_kernel(const JkSchwarzArgs args)
 #pragma unroll
             for (int k = 0; k < S::EPT; ++k) T[k] = 0.0;
             jk_quartet<LA, LB, LA, LB, NPA, NPB, NPA, NPB, GA, GB, GC, GD, double, 0, NTC>(
-                pr, pr, -1.0f, 0.0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
+                pr, pr, -1.0f, 0.0, 0, args.pp64, args.rys64, grp, 0u, tg, act, off, T);
             double mx = 0.0;
             if (act && ga == gc && gb == gd) {
 #pragma unroll

@@ -57,6 +57,16 @@ struct JkMol {
 struct JkRouterDev;
 struct JkPairFeat;
 
+// A band quartet the learned router released from the FP64 tier: bra pair
+// `item` of the launch's bra class, ket pair `ket` of its ket class, and the
+// density factor its screening used. The FP32 list kernel (MODE 3) of the
+// same class pair evaluates it.
+struct alignas(16) JkRouted {
+    int item, ket;
+    float dmq;
+    int pad;
+};
+
 // Arguments of one class-pair launch (passed by value).
 struct JkClassArgs {
     const JkPair *bra;           // pairs of the bra class
@@ -101,6 +111,16 @@ struct JkClassArgs {
     float *log_y;                // MODE 2: labels
     unsigned long long *log_n;   // MODE 2: samples written (may exceed log_cap)
     long long log_cap;
+    // routed builds: the FP64 tier (MODE 1) appends the band quartets the
+    // router releases to this launch's list (while it has room; a quartet
+    // that finds it full stays in FP64); the FP32 list kernel (MODE 3) of the
+    // class pair evaluates min(*rcount, rcap) entries
+    JkRouted *rlist;
+    unsigned long long *rcount;
+    long long rcap;
+    // 1: the FP32 tier evaluates the large-T (Gauss-Hermite) roots and
+    // weights in FP64 and rounds them to FP32
+    int asym64;
 };
 
 // Arguments of the Schwarz (diagonal-quartet) launch of one pair class.

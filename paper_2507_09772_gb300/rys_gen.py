@@ -215,6 +215,9 @@ def write_sources(outdir: str) -> dict:
         for i in range(0, t64p.size, 4):
             f.write(",".join(_fmt(v) for v in t64p[i:i + 4]) + ",\n")
         f.write("};\n")
+        f.write(f"static const int rys32_nint_host[{NMAX + 1}] = {{0,"
+                + ",".join(str(p['nint']) for p in p32) + "};\n")
+        f.write(f"static const int rys32_deg_host = {p32[0]['deg']};\n")
         f.write(f"static const size_t rys_table32_size = {t32.size};\n")
         f.write("static const double rys_table32_src[] = {\n")
         for i in range(0, t32.size, 4):
@@ -240,6 +243,9 @@ def write_sources(outdir: str) -> dict:
                     + ",".join(_fmt(p['tmax']) for p in ps) + "};\n")
             f.write(f"__device__ __constant__ int rys{tag}_nint[{NMAX + 1}] = {{0,"
                     + ",".join(str(p['nint']) for p in ps) + "};\n")
+        # compile-time interval counts of the FP32 tables (shared-memory sizing)
+        f.write(f"constexpr int rys32_nint_c[{NMAX + 1}] = {{0,"
+                + ",".join(str(p['nint']) for p in p32) + "};\n")
         # Gauss-Hermite limits, packed per N: x_r^2 then w_r
         offs, flat = [0], []
         for p in p64:

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "1", "--nmol", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", "1", "--nmol", "3", "--oracle-sample", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -25,8 +25,27 @@ def test_reference_arm_prints_one_json_line():
 def test_roofline_traffic_is_null_for_changed_or_unknown_kernels():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.traffic_for("jk_class_kernel<(00|00) prims 1111, fp64>", 1) is None
-    # a recorded entry is returned only while the kernel sources hash to the recorded value
-    label, g = next(iter(bench.TRAFFIC_BYTES))
-    got = bench.traffic_for(label, g)
-    assert got is None or got == bench.TRAFFIC_BYTES[(label, g)]
+    assert bench.traffic_for(7, 1000) is None   # no such tier
+    # recorded bytes are used only while the kernel sources hash to the capture's value
+    for tier, per_q in bench.TRAFFIC_BYTES_PER_QUARTET.items():
+        got = bench.traffic_for(tier, 1000)
+        if bench.sources_sha() == bench.TRAFFIC_SHA:
+            assert got == per_q * 1000
+        else:
+            assert got is None
+
+
+def test_family_roofline_arithmetic():
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = [dict(la=1, lb=0, lc=0, ld=0, na=1, nb=3, nc=3, nd=1, tier=0, threads_per_quartet=1, regs=100,
+                 ms=2.0, flops_model=2e9, quartets=10, launches=1),
+            dict(la=0, lb=0, lc=0, ld=0, na=3, nb=3, nc=3, nd=1, tier=0, threads_per_quartet=1, regs=80,
+                 ms=6.0, flops_model=3e9, quartets=30, launches=1),
+            dict(la=0, lb=0, lc=0, ld=0, na=3, nb=3, nc=3, nd=1, tier=1, threads_per_quartet=1, regs=60,
+                 ms=1.0, flops_model=9e9, quartets=99, launches=1)]
+    r = bench.family_roofline(rows, 0, 1.0e12, 10.0)
+    assert r["achieved"] == (5e9 / 8e-3) / 1e12 and r["launches"] == 2 and r["launch_ms"] == 4.0
+    assert abs(r["frac"] - (5e9 / 8e-3) / bench.PEAK_FP64_NOMINAL) < 1e-15
+    assert r["kernel_share"] == 0.8 and r["largest_class"]["class"] == "(00|00)/3331"
+    assert bench.family_roofline(rows, 1, None, 10.0)["achieved"] == 9.0

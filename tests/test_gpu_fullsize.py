@@ -89,18 +89,19 @@ def test_highl_cluster_cartesian_sampled_blocks():
     _compare(mol, J.cpu().numpy(), K.cpu().numpy(), jb, kb, TOL64)
 
 
-def _near_and_random_pairs(mol, rng, n_near, n_rand):
+def _near_and_random_pairs(mol, rng, n_near, n_rand, lmax=4):
     """Shell pairs: n_near with both shells within 2.5 bohr (large Q_ab, the
-    blocks that carry most of J), n_rand uniform."""
-    ns = mol.nshell
+    blocks that carry most of J), n_rand uniform; shells of l <= lmax (the
+    oracle's cost of a block grows steeply with its angular momenta)."""
+    ok = np.nonzero(mol.shells[:, 1] <= lmax)[0]
     xyz = np.asarray(mol.coords)[mol.shells[:, 0]]
     out = []
     while len(out) < n_near:
-        a = int(rng.integers(ns))
-        near = np.nonzero(np.linalg.norm(xyz - xyz[a], axis=1) < 2.5)[0]
+        a = int(rng.choice(ok))
+        near = ok[np.linalg.norm(xyz[ok] - xyz[a], axis=1) < 2.5]
         out.append((a, int(rng.choice(near))))
     for _ in range(n_rand):
-        out.append((int(rng.integers(ns)), int(rng.integers(ns))))
+        out.append((int(rng.choice(ok)), int(rng.choice(ok))))
     return np.array(out, dtype=np.int64)
 
 
@@ -159,8 +160,8 @@ def test_highl_cluster_spherical_mixed_sampled_blocks():
     cart.shells[:, 5] = 0
     Dc = np.einsum("ip,npq,jq->nij", C, mol.D, C)
     rng = np.random.default_rng(3)
-    jb = _near_and_random_pairs(cart, rng, 3, 1)
-    kb = _near_and_random_pairs(cart, rng, 3, 1)
+    jb = _near_and_random_pairs(cart, rng, 1, 1, lmax=1)
+    kb = _near_and_random_pairs(cart, rng, 1, 1, lmax=1)
     Jl, Kl, _ = oracle.jk_blocks(cart, jb, kb, D=Dc, cutoff=1e-13)
     offc = np.cumsum([0] + [oracle.ncart(int(l)) for l in mol.shells[:, 1]])
     offs = np.cumsum([0] + [2 * int(l) + 1 for l in mol.shells[:, 1]])

@@ -91,3 +91,28 @@ def test_split_precision_evaluation_matches_exact_rule(tables, N):
         u, W = rys_gen.evaluate_split(packed, params, N, T)
         assert np.max(np.abs(u / ue - 1)) < 6e-14
         assert np.max(np.abs(W / We - 1)) < 6e-14
+
+
+@pytest.mark.parametrize("N", range(1, 10))
+def test_fp32_large_T_limit_has_no_cancellation(N):
+    """The FP32 tier evaluates the Gauss-Hermite limit u = x^2 / T,
+    w = w_h / sqrt(T) in single precision from s = rsqrtf(T) (at most 2 ulp,
+    CUDA's documented bound). Emulated here with s off by 2 ulp either way
+    and every product rounded to FP32: u and w stay within 6 ulp of the FP64
+    value (products only, no cancellation), just above the table's end and
+    far beyond it."""
+    xh, wh = rys_gen.hermite_half(N)
+    x2 = (xh * xh).astype(np.float32)
+    whf = wh.astype(np.float32)
+    tmax = rys_gen.fit_tables(rys_gen.FP32_FIT, nmax=N)[1][N - 1]["tmax"]
+    ulp = 2.0 ** -23
+    for T in (tmax * (1 + 1e-6), tmax * 1.5, 1e3, 1e6):
+        s64 = 1.0 / math.sqrt(T)
+        for k in (-2, 0, 2):
+            s32 = np.float32(np.float32(s64) * np.float32(1 + k * ulp))
+            u32 = np.float32(x2 * np.float32(s32 * s32))
+            w32 = np.float32(whf * s32)
+            u64 = xh * xh / T
+            w64 = wh * s64
+            assert np.all(np.abs(u32 / u64 - 1) <= 6 * ulp), (N, T, k)
+            assert np.all(np.abs(w32 / w64 - 1) <= 6 * ulp), (N, T, k)
