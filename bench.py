@@ -135,6 +135,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
     ap.add_argument("--forms", default="mixed,routed", help="accelerated forms timed against the FP64 build")
     ap.add_argument("--chunk", type=int, default=0, help="candidate kets per work item (0: the library default)")
+    ap.add_argument("--chunk-fp64tier", type=int, default=0,
+                    help="the same for the FP64 tier of mixed and routed builds (0: the library default)")
     ap.add_argument("--oracle-blocks", type=int, default=8,
                     help="single large molecules: J and K shell blocks the oracle computes to check every form")
     ap.add_argument("--form-steps", type=int, default=2)
@@ -142,6 +144,8 @@ def parse():
     ap.add_argument("--graph", type=int, default=1, help="replay each build as one CUDA graph")
     ap.add_argument("--branches", type=int, default=4, help="class kernels forked over this many graph branches")
     ap.add_argument("--micro", action="store_true", help="appendix-style micro-benchmarks instead of the workload")
+    ap.add_argument("--micro-units", type=int, default=64,
+                    help="triatomic units of the d-only / f-only n_dm sweep geometry (3 atoms each)")
     ap.add_argument("--micro-cases", default="ss,d,f,forms",
                     help="micro-benchmark parts: ss ((ss|ss) n_prim sweep), d, f (n_dm sweeps), forms (the rest)")
     ap.add_argument("--tune", type=int, default=1, help="autotune the fragment shapes before the warm-up (untimed)")
@@ -435,6 +439,16 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets
                     out[name]["cost_vs_mixed"] = out[name]["ms_per_step"] / ref_mixed - 1.0
             finally:
                 eng.set_option(opt, 0)
+    # tau32 calibration: "mixed@<tau32>" times the mixed build at that threshold
+    for name in forms:
+        if name.startswith("mixed@"):
+            tau = float(name.split("@", 1)[1])
+            eng.set_option("tau32", tau)
+            try:
+                out[name] = timed("mixed")
+                out[name]["tau32"] = tau
+            finally:
+                eng.set_option("tau32", args.tau32)
     if "routed" in forms:
         # router: labels from FP64 logging builds of held-out molecules shaped
         # like the batched and cluster workloads (not the ones timed here),
@@ -503,6 +517,8 @@ def run_ours(args):
     eng.set_option("branches", args.branches)
     if args.chunk:
         eng.set_option("chunk", args.chunk)
+    if args.chunk_fp64tier:
+        eng.set_option("chunk_fp64tier", args.chunk_fp64tier)
     Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
     Js = [torch.empty_like(d) for d in Ds]
     Ks = [torch.empty_like(d) for d in Ds]
@@ -656,6 +672,8 @@ def run_ours(args):
                        "precision": args.precision, "cutoff": args.cutoff,
                        "l2": "flushed before every step (256 MiB write)",
                        "graph": args.graph, "branches": args.branches,
+                       "chunk": eng.get_option("chunk"), "chunk_fp64tier": eng.get_option("chunk_fp64tier"),
+                       "screen64": eng.get_option("screen64"),
                        "parallelism": f"{ws} independent batch(es), one per GPU"},
             "quartets_per_step": quartets / args.steps,
             "prim_quartets_per_step": sum(s["prim_quartets"] for s in stats) / args.steps,
@@ -733,7 +751,7 @@ def run_micro(args):
         rows.append({"case": "(ss|ss)", "natm": len(xyz), "n_prim": n, "ms_fp64": m64, "ms_fp32": m32,
                      "fp64_over_fp32": m64 / m32, "quartets": s64["quartets_fp64"],
                      "prim_quartets": s64["prim_quartets"]})
-    xyz = geometry(64, 2002)
+    xyz = geometry(args.micro_units, 2002)
     for l, name in ((2, "d-only"), (3, "f-only")):
         if name[0] not in cases:
             continue

@@ -160,9 +160,9 @@ int jk_init_batch(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *sh
 
 /* J and K for a single-molecule handle (see the conventions above).
  * cutoff: quartets with Q_ab Q_cd Dmax <= cutoff are skipped (the paper uses
- * 1e-13); for cutoff >= 1e-30 the bound and the tier thresholds are compared
- * in FP32 (every tier alike, so each quartet runs exactly once), below it in
- * FP64. precision_mode: JK_PREC_*. stats may be NULL. */
+ * 1e-13); the bound and the tier thresholds are compared in FP64 (option
+ * "screen64" = 0: in FP32 for cutoff >= 1e-30, every tier alike, so each
+ * quartet still runs exactly once). precision_mode: JK_PREC_*. stats may be NULL. */
 int jk_build(jk_handle *h, const double *D, int32_t n_dm, int with_j, int with_k, double cutoff,
              int precision_mode, double *J, double *K, void *stream, jk_stats *stats);
 
@@ -191,16 +191,21 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * combines GPUs that split one batch),
  * "branches" (1..8: class kernels forked over this many streams / graph
  * branches),
- * "chunk" (32..4096, default 64: candidate kets per work item of the
+ * "chunk" (32..65536, default 64: candidate kets per work item of the
  * persistent class kernels; changing it re-plans the work items),
  * "asym64" (0/1, default 0: the FP32 tier evaluates the large-T
  * Gauss-Hermite limit of the Rys roots and weights in FP64 and rounds the
  * result to FP32, instead of evaluating it in FP32),
- * "screen64" (0/1, default 0: compare the screening bounds, tier thresholds
- * and the primitive threshold in FP64 whatever the cutoff),
- * "route_cap" (default 16777216: entries of the per-class-pair lists of
- * quartets the router releases from the FP64 tier, shared out by estimated
- * work; a released quartet that finds its list full stays in FP64). With "use_graph" = 1 the first build of a flag combination is
+ * "chunk_fp64tier" (default 64: the same for the FP64 tier of mixed and
+ * routed builds, whose kernels keep only the candidates above tau32),
+ * "screen64" (0/1, default 1: compare the screening bounds, tier thresholds
+ * and the primitive threshold in FP64; 0 compares them in FP32 when the
+ * cutoff is >= 1e-30),
+ * "route_cap" (default 16777216: initial entries of the per-class-pair lists
+ * of quartets the router releases from the FP64 tier, shared out by
+ * candidate count; a list that overflowed in a build with stats is grown
+ * for the next build; a released quartet that finds its list full stays in
+ * FP64). With "use_graph" = 1 the first build of a flag combination is
  * captured into a CUDA graph on an internal stream and replayed on `stream`
  * by later builds; the per-call D/J/K pointers are read from a device
  * descriptor copied before each launch, so changing buffers is allowed.

@@ -693,14 +693,18 @@ struct Launch {
     int c1, c2;        // pair classes (bra, ket)
     KSpec spec[2];     // [0] FP64, [1] FP32
     double cost;       // scheduling estimate
-    long long *d_prefix = nullptr;  // nbra + 1 work-item offsets (chunks of kets per bra)
-    long long nitems = 0;
+    // nbra + 1 work-item offsets (chunks of kets per bra): [0] with the
+    // handle's chunk, [1] with the chunk of the FP64 tier of two-tier builds
+    long long *d_prefix[2] = {nullptr, nullptr};
+    long long nitems[2] = {0, 0};
+    double cand = 0;   // candidate kets summed over the bras (Q_ab Q_cd > JK_ITEM_EPS)
 };
 
 // Kets per work item. A bra pair's candidate kets (those whose Schwarz
 // product can exceed JK_ITEM_EPS with Dmax = 1) are split into chunks of this
 // size; the last chunk always runs to the molecule's last ket.
 #define JK_CHUNK 64
+#define JK_CHUNK_HI 64
 #define JK_ITEM_EPS 1e-15
 
 }  // namespace
@@ -776,10 +780,14 @@ struct jk_handle {
     JkRouted *d_rlist = nullptr;           // routed builds: released quartets, per launch segments
     unsigned long long *d_rcount = nullptr;
     std::vector<long long> rl_off, rl_cap;
+    std::vector<long long> rl_need;        // entries each list needed in the last build with stats
     double route_cap = 16777216.0;         // list entries over all launches
     int asym64 = 0;                        // FP32 tier: large-T roots and weights in FP64
     int chunk = 64;                        // kets per work item
-    int screen64 = 0;                      // bounds compared in FP64 whatever the cutoff
+    int chunk_hi = 64;                     // ... for the FP64 tier of mixed and routed builds
+    // bounds compared in FP64 (0: in FP32 when the cutoff is >= 1e-30); FP64
+    // costs about 2 % of a mixed build of the batched workload
+    int screen64 = 1;
     // graphs and branch streams
     int branches = 1;
     cudaStream_t cap = nullptr;
@@ -794,7 +802,7 @@ void free_handle(jk_handle *h)
 {
     if (!h) return;
     for (auto &c : h->classes) { cudaFree(c.d_beg); cudaFree(c.d_end); }
-    for (auto &L : h->launches) cudaFree(L.d_prefix);
+    for (auto &L : h->launches) { cudaFree(L.d_prefix[0]); cudaFree(L.d_prefix[1]); }
     cudaFree(h->d_sh_mol); cudaFree(h->d_mol_sh0); cudaFree(h->d_sh_ao); cudaFree(h->d_sh_nc);
     cudaFree(h->d_pairs); cudaFree(h->d_pp64); cudaFree(h->d_pp32); cudaFree(h->d_mols);
     cudaFree(h->d_dmax); cudaFree(h->d_dmax32); cudaFree(h->d_dmax_mol); cudaFree(h->d_rys64); cudaFree(h->d_rys32);
@@ -835,13 +843,16 @@ long type_key(const jk_shell &s) { return (long)s.l * 64 + s.nprim; }
 
 // Work items of every launch: per bra, ceil(candidates / chunk) (at least
 // one), where the candidates are the kets (sorted by Q) with Q_ab Q_cd >
-// JK_ITEM_EPS; the last chunk of a bra runs to the molecule's last ket. Also
-// the launch's cost estimate (candidates x modelled FLOPs per quartet).
-int plan_items(jk_handle *h, int chunk)
+// JK_ITEM_EPS; the last chunk of a bra runs to the molecule's last ket. Two
+// partitions: `chunk` for every tier but one, `chunk_hi` for the FP64 tier
+// of mixed and routed builds, which keeps only the few candidates above
+// tau32, so that its items still fill whole rounds of a warp. Also the
+// launch's cost estimate (candidates x modelled FLOPs per quartet).
+int plan_items(jk_handle *h, int chunk, int chunk_hi)
 {
     for (auto &L : h->launches) {
         const PairClass &A = h->classes[L.c1], &B = h->classes[L.c2];
-        std::vector<long long> pre(A.n + 1, 0);
+        std::vector<long long> pre(A.n + 1, 0), pre2(A.n + 1, 0);
         double work = 0;
         for (int m = 0; m < h->nmol; ++m) {
             const int b0 = A.beg[m], b1 = A.end[m];
@@ -856,19 +867,22 @@ int plan_items(jk_handle *h, int chunk)
                     if (qa * h->h_pairs[B.off + mid].Q > JK_ITEM_EPS) lo = mid + 1; else hi = mid;
                 }
                 long long ncand = std::max(0, lo - kfirst);
-                long long nch = std::max(1LL, (ncand + chunk - 1) / chunk);
-                pre[bi + 1] = nch;
+                pre[bi + 1] = std::max(1LL, (ncand + chunk - 1) / chunk);
+                pre2[bi + 1] = std::max(1LL, (ncand + chunk_hi - 1) / chunk_hi);
                 work += (double)ncand;
             }
         }
-        for (int bi = 0; bi < A.n; ++bi) pre[bi + 1] += pre[bi];
-        L.nitems = pre[A.n];
-        cudaFree(L.d_prefix);
-        L.d_prefix = nullptr;
-        if (int rc = upload(&L.d_prefix, pre)) return rc;
+        for (int bi = 0; bi < A.n; ++bi) { pre[bi + 1] += pre[bi]; pre2[bi + 1] += pre2[bi]; }
+        L.nitems[0] = pre[A.n];
+        L.nitems[1] = pre2[A.n];
+        for (int t = 0; t < 2; ++t) { cudaFree(L.d_prefix[t]); L.d_prefix[t] = nullptr; }
+        if (int rc = upload(&L.d_prefix[0], pre)) return rc;
+        if (int rc = upload(&L.d_prefix[1], pre2)) return rc;
+        L.cand = work;
         L.cost = work * class_flops(L.spec[0], 1);
     }
     h->chunk = chunk;
+    h->chunk_hi = chunk_hi;
     return JK_OK;
 }
 
@@ -1236,7 +1250,7 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
             }
             h->launches.push_back(L);
         }
-    if ((rc = plan_items(h.get(), JK_CHUNK))) return rc;
+    if ((rc = plan_items(h.get(), JK_CHUNK, JK_CHUNK_HI))) return rc;
     std::stable_sort(h->launches.begin(), h->launches.end(), [](const Launch &x, const Launch &y) { return x.cost > y.cost; });
 
     // ---- per-build scratch
@@ -1409,19 +1423,31 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         ++h->cart_gen;
     }
     // routed builds: one list per class pair for the quartets the router
-    // releases from the FP64 tier, sized by the pair's share of the estimated
-    // work (at least 4,096 entries); a quartet that finds its list full stays
+    // releases from the FP64 tier, first sized by the pair's share of the
+    // candidate quartets (at least 4,096 entries), then grown to what a
+    // build with stats saw it need; a quartet that finds its list full stays
     // in FP64
-    if (routed && !h->d_rlist) {
+    bool grow = false;
+    if (routed && h->d_rlist)
+        for (size_t i = 0; i < h->rl_need.size(); ++i) grow = grow || h->rl_need[i] > h->rl_cap[i];
+    if (routed && (!h->d_rlist || grow)) {
         CK(cudaStreamSynchronize(st));
+        cudaFree(h->d_rlist); cudaFree(h->d_rcount);
+        h->d_rlist = nullptr; h->d_rcount = nullptr;
         double tc2 = 0;
-        for (auto &L : h->launches) tc2 += L.cost;
+        for (auto &L : h->launches) tc2 += L.cand;
+        std::vector<long long> cap(h->launches.size());
+        for (size_t i = 0; i < h->launches.size(); ++i) {
+            const double share = tc2 > 0 ? h->launches[i].cand / tc2 : 1.0 / h->launches.size();
+            cap[i] = std::max(4096LL, (long long)(h->route_cap * share));
+            if (i < h->rl_cap.size()) cap[i] = std::max(cap[i], h->rl_cap[i]);
+            if (i < h->rl_need.size() && h->rl_need[i] > cap[i]) cap[i] = h->rl_need[i] + h->rl_need[i] / 4 + 4096;
+        }
         h->rl_off.assign(h->launches.size(), 0);
-        h->rl_cap.assign(h->launches.size(), 0);
+        h->rl_cap = cap;
+        h->rl_need.assign(h->launches.size(), 0);
         long long tot = 0;
         for (size_t i = 0; i < h->launches.size(); ++i) {
-            const double share = tc2 > 0 ? h->launches[i].cost / tc2 : 1.0 / h->launches.size();
-            h->rl_cap[i] = std::max(4096LL, (long long)(h->route_cap * share));
             h->rl_off[i] = tot;
             tot += h->rl_cap[i];
         }
@@ -1586,11 +1612,12 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.log_n = h->d_logn;
             a.log_cap = logs ? logs->cap : 0;
             a.nbra = A.n;
-            a.item_prefix = L.d_prefix;
-            const long long nunits = L.nitems * specs[k].gx;   // work items x slabs
+            const int pi = (tier[k] == 0 && (mode == JK_PREC_MIXED || routed)) ? 1 : 0;
+            a.item_prefix = L.d_prefix[pi];
+            const long long nunits = L.nitems[pi] * specs[k].gx;   // work items x slabs
             a.item_lo = nunits * h->part_index / h->part_count;
             a.item_hi = nunits * (h->part_index + 1) / h->part_count;
-            a.chunk = h->chunk;
+            a.chunk = pi ? h->chunk_hi : h->chunk;
             a.prim_eps = std::min(cutoff, h->prim_eps);
             a.prim_eps32 = (float)a.prim_eps;
             a.omega = std::fabs(h->omega);
@@ -1675,6 +1702,11 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         CK(cudaMemcpy(cnt.data(), h->d_stats, sizeof(unsigned long long) * 3 * nl, cudaMemcpyDeviceToHost));
         int err = 0;
         CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (routed) {
+            std::vector<unsigned long long> rc2(h->launches.size());
+            CK(cudaMemcpy(rc2.data(), h->d_rcount, sizeof(unsigned long long) * rc2.size(), cudaMemcpyDeviceToHost));
+            h->rl_need.assign(rc2.begin(), rc2.end());
+        }
         memset(stats, 0, sizeof(*stats));
         int64_t routed_fp32 = 0;
         stats->ms = ms;
@@ -1842,7 +1874,7 @@ int tune_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int
     std::vector<Item> items;
     for (size_t l = 0; l < h->launches.size(); ++l) {
         const Launch &L = h->launches[l];
-        if (L.nitems == 0 || L.cost < min_share * total) continue;
+        if (L.nitems[0] == 0 || L.cost < min_share * total) continue;
         for (int t : tiers) {
             Item it;
             it.l = (int)l;
@@ -2045,13 +2077,14 @@ int jk_set_option(jk_handle *h, const char *key, double value)
         h->branches = (int)value;
     }
     else if (k == "asym64") h->asym64 = value != 0;
-    else if (k == "chunk") {
-        if (!(value >= 32 && value <= 4096)) return fail(JK_ERR_ARG, "chunk must be in [32, 4096]");
-        if ((int)value != h->chunk) {
+    else if (k == "chunk" || k == "chunk_fp64tier") {
+        if (!(value >= 32 && value <= 65536)) return fail(JK_ERR_ARG, "%s must be in [32, 65536]", key);
+        const int c0 = k == "chunk" ? (int)value : h->chunk, c1 = k == "chunk" ? h->chunk_hi : (int)value;
+        if (c0 != h->chunk || c1 != h->chunk_hi) {
             cudaDeviceSynchronize();
             for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
             h->graphs.clear();
-            if (int rc = plan_items(h, (int)value)) return rc;
+            if (int rc = plan_items(h, c0, c1)) return rc;
         }
     }
     else if (k == "screen64") h->screen64 = value != 0;
@@ -2061,6 +2094,7 @@ int jk_set_option(jk_handle *h, const char *key, double value)
             cudaDeviceSynchronize();
             cudaFree(h->d_rlist); cudaFree(h->d_rcount);
             h->d_rlist = nullptr; h->d_rcount = nullptr;
+            h->rl_cap.clear(); h->rl_need.clear();
             for (auto &g : h->graphs) cudaGraphExecDestroy(g.second.first);
             h->graphs.clear();
         }
@@ -2087,6 +2121,7 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "part_index") *value = h->part_index;
     else if (k == "asym64") *value = h->asym64;
     else if (k == "chunk") *value = h->chunk;
+    else if (k == "chunk_fp64tier") *value = h->chunk_hi;
     else if (k == "screen64") *value = h->screen64;
     else if (k == "route_cap") *value = h->route_cap;
     else if (k == "graphs") *value = (double)h->graphs.size();

@@ -11,10 +11,11 @@
 // each layer (normalised features, hidden activations) are rounded to BF16;
 // the training kernels and the CPU reference round the same way.
 //
-// This header is compiled into the runtime-compiled integral kernels (both
-// tiers) and into the library's training kernels. Every step is either an
-// MMA (fixed accumulation order) or an explicitly rounded intrinsic, so the
-// FP64 and FP32 tier kernels reach bit-identical decisions for a quartet.
+// This header is compiled into the runtime-compiled integral kernels (the
+// FP64 tier of routed builds runs it) and into the library's training
+// kernels. Every step is either an MMA (fixed accumulation order) or an
+// explicitly rounded intrinsic, so a quartet's decision does not depend on
+// the kernel or the launch that evaluates it.
 #pragma once
 
 #define JK_RT_NIN 12
