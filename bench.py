@@ -242,10 +242,18 @@ def cpu_oracle_sample(mols, seconds: float, cutoff: float, quartets_per_step=Non
     whole step is extrapolated from the rate and labelled so."""
     import numpy as np
     import oracle
-    if len(mols) == 1 and mols[0].natm > 100:
+    if len(mols) == 1:
         mol = mols[0]
         if mol.spherical:
-            return None
+            # the oracle works in the Cartesian basis: time it on the
+            # Cartesian twin with D_cart = C D C^T
+            from paper_2507_09772_gb300 import synth
+            C = oracle.c2s_matrix(mol)
+            sh = mol.shells.copy()
+            sh[:, 5] = 0
+            mol = synth.Molecule(coords=mol.coords, shells=sh, exps=mol.exps, coeffs=mol.coeffs,
+                                 nao=mol.nao_cart, nao_cart=mol.nao_cart,
+                                 D=np.stack([C @ d @ C.T for d in mol.D]), name=mol.name + "-cart")
         Q = oracle.schwarz_coulomb(mol)
         rng = np.random.default_rng(0)
         nq, t_total, nb = 0, 0.0, 0
@@ -377,8 +385,9 @@ def oracle_blocks(mol, nblocks, cutoff, seed=7):
 
 def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets, ocmp=None):
     """The accelerated forms listed in --forms (mixed: Schwarz x Dmax tiering;
-    mixed_asym64, mixed_screen64: the same with the FP32 tier's large-T Rys
-    limit, or every bound, in FP64; routed: the learned router in the band)
+    mixed_asym64: the same with the FP32 tier's large-T Rys limit in FP64;
+    mixed_screen32: with the bounds compared in plain FP32; routed: the
+    learned router in the band; mixed@<tau32>: another FP32 threshold)
     on the same inputs, timed like the base build (--precision), with their
     largest deviation from the base build over every element of J and K (and,
     for a single large molecule, from the oracle on sampled shell blocks)."""
@@ -428,17 +437,18 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets
         out["mixed"]["autotune"] = tune
         out["mixed"]["tiers"] = tier_split(eng, Ds, Js, Ks, args, "mixed")
     # the mixed build with the large-T Rys limit of the FP32 tier in FP64
-    # (asym64) and with every bound compared in FP64 (screen64)
+    # (asym64 = 1), and with the bounds compared in plain FP32 (screen64 = 0)
     ref_mixed = out["mixed"]["ms_per_step"] if "mixed" in out else (base_ms if base == "mixed" else None)
-    for name, opt in (("mixed_asym64", "asym64"), ("mixed_screen64", "screen64")):
+    for name, opt, val in (("mixed_asym64", "asym64", 1), ("mixed_screen32", "screen64", 0)):
         if name in forms:
-            eng.set_option(opt, 1)
+            old = eng.get_option(opt)
+            eng.set_option(opt, val)
             try:
                 out[name] = timed("mixed")
                 if ref_mixed:
                     out[name]["cost_vs_mixed"] = out[name]["ms_per_step"] / ref_mixed - 1.0
             finally:
-                eng.set_option(opt, 0)
+                eng.set_option(opt, old)
     # tau32 calibration: "mixed@<tau32>" times the mixed build at that threshold
     for name in forms:
         if name.startswith("mixed@"):

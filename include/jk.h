@@ -196,7 +196,7 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * "asym64" (0/1, default 0: the FP32 tier evaluates the large-T
  * Gauss-Hermite limit of the Rys roots and weights in FP64 and rounds the
  * result to FP32, instead of evaluating it in FP32),
- * "chunk_fp64tier" (default 64: the same for the FP64 tier of mixed and
+ * "chunk_fp64tier" (default 512: the same for the FP64 tier of mixed and
  * routed builds, whose kernels keep only the candidates above tau32),
  * "screen64" (0/1, default 1: compare the screening bounds, tier thresholds
  * and the primitive threshold in FP64; 0 compares them in FP32 when the

@@ -309,14 +309,14 @@ def _to_cart_density(mol, D):
         D = D[None]
     if mol.spherical:
         C = c2s_matrix(mol)
-        D = np.einsum("ip,npq,jq->nij", C, D, C)
+        D = np.stack([C @ d @ C.T for d in D])   # D_cart = C D_sph C^T
     return np.ascontiguousarray(D)
 
 
 def _from_cart(mol, M):
     if mol.spherical:
         C = c2s_matrix(mol)
-        M = np.einsum("ip,nij,jq->npq", C, M, C)
+        M = np.stack([C.T @ m @ C for m in M])   # X_sph = C^T X_cart C
     return M
 
 

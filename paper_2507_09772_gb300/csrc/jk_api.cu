@@ -704,7 +704,9 @@ struct Launch {
 // product can exceed JK_ITEM_EPS with Dmax = 1) are split into chunks of this
 // size; the last chunk always runs to the molecule's last ket.
 #define JK_CHUNK 64
-#define JK_CHUNK_HI 64
+// The FP64 tier of a mixed build keeps ~7 % of the candidates; with 512 per
+// item the batched mixed build ran 5 % faster than with 64 (and than 2,048).
+#define JK_CHUNK_HI 512
 #define JK_ITEM_EPS 1e-15
 
 }  // namespace
@@ -1033,8 +1035,9 @@ int init_impl(int32_t nmol, const int32_t *mol_shell_off, const jk_shell *shells
         p.a_ao = h->sh_ao_cart[a]; p.b_ao = h->sh_ao_cart[b];
         p.a_loc = a - mol_shell_off[p.mol]; p.b_loc = b - mol_shell_off[p.mol];
         const double *A = coords + 3 * shells[a].atom, *B = coords + 3 * shells[b].atom;
-        p.Ax = A[0]; p.Ay = A[1]; p.Az = A[2];
         p.ABx = A[0] - B[0]; p.ABy = A[1] - B[1]; p.ABz = A[2] - B[2];
+        p.ABxf = (float)p.ABx; p.AByf = (float)p.ABy; p.ABzf = (float)p.ABz;
+        p.pad0 = 0; p.pad1 = 0.0;
         p.Q = 0; p.Qf = 0.f; p.padf = 0.f;
     }
     JkPair *d_cp = nullptr;
@@ -1597,7 +1600,10 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             // FP32 screening unless the cutoff is below the FP32 range; one
             // choice for every launch of the build, so that the tiers of a
             // mixed build compare the same bounds in the same precision
-            a.scr32 = (cutoff >= 1e-30 && !h->screen64) ? 1 : 0;
+            // screening: FP32 bounds with the FP64 rule kept exact (2, the
+            // default), plain FP32 (1, option screen64 = 0), or FP64 (0, for
+            // cutoffs below the FP32 range)
+            a.scr32 = cutoff >= 1e-30 ? (h->screen64 ? 2 : 1) : 0;
             a.lo32 = (float)a.lo;
             a.hi32 = std::isinf(a.hi) ? INFINITY : (float)a.hi;
             a.tau32 = (float)tau;

@@ -49,6 +49,45 @@ __device__ __forceinline__ float jk_pp_q(const JkPrimPair64 &r) { return r.qf; }
 __device__ __forceinline__ float jk_pp_q(const JkPrimPair32 &r) { return r.q; }
 
 __device__ __forceinline__ double jk_rsqrt(double x) { return rsqrt(x); }
+
+// A - B of a pair in the tier's precision (the FP32 copy is stored, so the
+// FP32 tier converts nothing on the FP64 pipe).
+__device__ __forceinline__ void jk_pair_ab(const JkPair &p, double &x, double &y, double &z)
+{
+    x = p.ABx; y = p.ABy; z = p.ABz;
+}
+__device__ __forceinline__ void jk_pair_ab(const JkPair &p, float &x, float &y, float &z)
+{
+    x = p.ABxf; y = p.AByf; z = p.ABzf;
+}
+
+// An FP32 tier contribution widened to FP64 for the FP64 atomics into J and
+// K. A float-to-double conversion is an FP64-pipe instruction (1/64 of the
+// FP32 rate on GB300, as costly as the FP32 arithmetic of a whole small
+// quartet), so the FP32 tier builds the IEEE-754 binary64 bit pattern with
+// integer operations instead: sign, exponent rebiased from 127 to 1023,
+// fraction shifted left by 29; subnormal floats are normalised first. Exact
+// for every float.
+__device__ __forceinline__ double jk_to_f64(double x) { return x; }
+__device__ __forceinline__ double jk_to_f64(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) {
+        bits = sgn | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    } else if (e != 0) {
+        bits = sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0) {
+        bits = sgn;
+    } else {
+        const int top = 31 - __clz(m);   // leading bit of the subnormal fraction, 0..22
+        bits = sgn | ((unsigned long long)(top + 874) << 52) |
+               (((unsigned long long)m << (52 - top)) & 0xfffffffffffffull);
+    }
+    return __longlong_as_double((long long)bits);
+}
 __device__ __forceinline__ float jk_rsqrt(float x) { return rsqrtf(x); }
 
 // ----------------------------------------------------- Rys roots, weights
@@ -306,8 +345,9 @@ __device__ __forceinline__ int jk_quartet(const JkPair &bra, const JkPair &ket, 
     typedef typename JkPP<R>::T PPT;
     constexpr int NR = S::NR;
     constexpr int NRE = S::NRE;
-    const R ABx = (R)bra.ABx, ABy = (R)bra.ABy, ABz = (R)bra.ABz;
-    const R CDx = (R)ket.ABx, CDy = (R)ket.ABy, CDz = (R)ket.ABz;
+    R ABx, ABy, ABz, CDx, CDy, CDz;
+    jk_pair_ab(bra, ABx, ABy, ABz);
+    jk_pair_ab(ket, CDx, CDy, CDz);
     const PPT *bpp = pp + bra.pp_off;
     const PPT *kpp = pp + ket.pp_off;
     // primitive pairs are sorted by their Schwarz factor q (largest first):
@@ -454,22 +494,23 @@ __device__ __forceinline__ bool jk_route_out(const JkClassArgs &args, bool rel, 
 // ------------------------------------------------- screening of a candidate
 template <int MODE>
 __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
-                                                const double *dmx, double dmol, int j, int ke, bool &sig,
-                                                bool &stop, bool &band, float &dmq, float &Bout);
+                                                const double *dmx, double dmol, float dmol32, int j, int ke,
+                                                bool &sig, bool &stop, bool &band, float &dmq, float &Bout);
 // Keep (bra, ket j) iff lo < Q_ab Q_cd Dmax <= hi; `stop` when even the
 // molecule's largest density element cannot lift this ket (and every later
 // one, kets being sorted by Q) above lo.
 template <int MODE>
 __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair &bra, const JkPairFeat &braf,
-                                          const JkMol &mol, const double *dmx, double dmol, int item, int j, int ke,
-                                          bool &sig, bool &stop, bool &band, float &dmq, unsigned short *rsm)
+                                          const JkMol &mol, const double *dmx, double dmol, float dmol32, int item,
+                                          int j, int ke, bool &sig, bool &stop, bool &band, float &dmq,
+                                          unsigned short *rsm)
 {
     sig = false;
     stop = false;
     band = false;
     dmq = 1.0f;
     float B = 0.0f;
-    jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, j, ke, sig, stop, band, dmq, B);
+    jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, dmol32, j, ke, sig, stop, band, dmq, B);
     if (MODE == 1) {
         // learned router for the band candidates, all lanes together on the
         // tensor cores; `band` then marks the quartets released to FP32
@@ -485,23 +526,38 @@ __device__ __forceinline__ void jk_screen(const JkClassArgs &args, const JkPair 
     }
 }
 
+// Whether x and y (FP32 images of FP64 quantities, relative error at most
+// 5 FP32 roundings, 3.0e-7) are too close for their order to be decided in
+// FP32: then the caller redoes the comparison in FP64.
+__device__ __forceinline__ bool jk_near(float x, float y)
+{
+    return fabsf(x - y) < 2e-6f * y;   // false for y = infinity
+}
+
 template <int MODE>
 __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const JkPair &bra, const JkMol &mol,
-                                                const double *dmx, double dmol, int j, int ke, bool &sig,
-                                                bool &stop, bool &band, float &dmq, float &Bout)
+                                                const double *dmx, double dmol, float dmol32, int j, int ke,
+                                                bool &sig, bool &stop, bool &band, float &dmq, float &Bout)
 {
     if (j >= ke) return;
     const JkPair &kt = args.ket[j];
     if (args.scr32) {
-        // FP32 path: a handful of FP32 operations per candidate instead of
-        // FP64-pipe work (the FP32 tier's whole budget on GB300)
+        // FP32 bounds: a handful of FP32 operations per candidate instead of
+        // FP64-pipe work (an FP64 instruction costs the FP32 tier 64 FP32
+        // ones on GB300). scr32 == 2 keeps the FP64 rule exact: the FP32
+        // products carry at most 5 roundings, so only a bound within 2e-6 of
+        // a threshold can compare differently from its FP64 value, and those
+        // few are redone in FP64 (every tier decides alike, as in FP64).
         const float bq = bra.Qf * __ldg(&kt.Qf);
-        if (bq * (float)dmol <= args.lo32) { stop = true; return; }
+        const float s = bq * dmol32;
+        bool st = s <= args.lo32;
+        if (args.scr32 == 2 && jk_near(s, args.lo32)) st = (bra.Q * kt.Q) * dmol <= args.lo;
+        if (st) { stop = true; return; }
         float dm = 1.0f;
+        const int c = __ldg(&kt.a_loc), d = __ldg(&kt.b_loc);
+        const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
         if (args.use_dmax) {
             const float *d32 = args.dmax32 + mol.dmax_off;
-            const int c = __ldg(&kt.a_loc), d = __ldg(&kt.b_loc);
-            const int a = bra.a_loc, b = bra.b_loc, ns = mol.nsh;
             dm = 0.0f;
             if (args.with_j) dm = fmaxf(__ldg(d32 + a * ns + b), __ldg(d32 + c * ns + d));
             if (args.with_k) {
@@ -509,11 +565,28 @@ __device__ __forceinline__ void jk_screen_bound(const JkClassArgs &args, const J
                 dm = fmaxf(dm, fmaxf(__ldg(d32 + b * ns + c), __ldg(d32 + b * ns + d)));
             }
         }
+        // the FP32 image of the FP64 maximum is the maximum of the images
         dmq = dm;
         const float B = bq * dm;
         Bout = B;
         sig = (B > args.lo32) && (B <= args.hi32);
         band = MODE == 1 && sig && B > args.tau32 && B <= args.band_hi32;
+        if (args.scr32 == 2 &&
+            (jk_near(B, args.lo32) || jk_near(B, args.hi32) ||
+             (MODE == 1 && (jk_near(B, args.tau32) || jk_near(B, args.band_hi32))))) {
+            double dm64 = 1.0;
+            if (args.use_dmax) {
+                dm64 = 0.0;
+                if (args.with_j) dm64 = fmax(__ldg(dmx + a * ns + b), __ldg(dmx + c * ns + d));
+                if (args.with_k) {
+                    dm64 = fmax(dm64, fmax(__ldg(dmx + a * ns + c), __ldg(dmx + a * ns + d)));
+                    dm64 = fmax(dm64, fmax(__ldg(dmx + b * ns + c), __ldg(dmx + b * ns + d)));
+                }
+            }
+            const double B64 = (bra.Q * kt.Q) * dm64;
+            sig = (B64 > args.lo) && (B64 <= args.hi);
+            band = MODE == 1 && sig && B64 > args.tau && B64 <= args.band_hi;
+        }
         return;
     }
     const double bq = bra.Q * kt.Q;
@@ -620,7 +693,7 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
             for (int ic = 0; ic < FC; ++ic)
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, (double)((R)2 * f * jcd[ic][id]));
+                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, jk_to_f64((R)2 * f * jcd[ic][id]));
         }
         if (DOK) {
             R Dbd[FB][FD], Dbc[FB][FC], Dad[FA][FD], Dac[FA][FC];
@@ -672,19 +745,19 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
             for (int ia = 0; ia < FA; ++ia) {
 #pragma unroll
                 for (int ic = 0; ic < FC; ++ic)
-                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, (double)(f * kac[ia][ic]));
+                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, jk_to_f64(f * kac[ia][ic]));
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, (double)(f * kad[ia][id]));
+                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, jk_to_f64(f * kad[ia][id]));
             }
 #pragma unroll
             for (int ib = 0; ib < FB; ++ib) {
 #pragma unroll
                 for (int ic = 0; ic < FC; ++ic)
-                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, (double)(f * kbc[ib][ic]));
+                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, jk_to_f64(f * kbc[ib][ic]));
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, (double)(f * kbd[ib][id]));
+                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, jk_to_f64(f * kbd[ib][id]));
             }
         }
     }
@@ -701,7 +774,7 @@ __device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol 
 #pragma unroll
             for (int ib = 0; ib < FB; ++ib)
                 if (jab[m][ia][ib] != (R)0)
-                    atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, (double)jab[m][ia][ib]);
+                    atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, jk_to_f64(jab[m][ia][ib]));
 }
 
 // Work item t -> bra pair i (binary search in the item prefix) and the ket
@@ -841,6 +914,7 @@ jk_class_kernel(const JkClassArgs args)
             const int ke = (ch == nch - 1) ? kend : min(kend, kb + args.chunk);
             const double *dmx = args.dmax + mol.dmax_off;
             const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
+            const float dmol32 = (float)dmol;
             const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
             JkPairFeat braf;
             if (MODE != 0) braf = args.bra_feat[item];
@@ -862,7 +936,7 @@ jk_class_kernel(const JkClassArgs args)
             for (int base = kb; base < ke; base += 32) {
                 bool sig = false, stop = false, band = false;
                 float dmq = 1.0f, B = 0.0f;
-                jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, base + lane, ke, sig, stop, band, dmq, B);
+                jk_screen_bound<MODE>(args, bra, mol, dmx, dmol, dmol32, base + lane, ke, sig, stop, band, dmq, B);
                 const unsigned lt = (1u << lane) - 1u;
                 const bool def = sig && !band;   // decided by the bounds alone
                 const unsigned mdef = __ballot_sync(0xffffffffu, def);
@@ -1072,6 +1146,7 @@ jk_class_kernel(const JkClassArgs args)
             const int ke = (ch == nch - 1) ? kend : min(kend, kb + args.chunk);
             const double *dmx = args.dmax + mol.dmax_off;
             const double dmol = args.use_dmax ? args.dmax_mol[bra.mol] : 1.0;
+            const float dmol32 = (float)dmol;
             const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
             JkPairFeat braf;
             if (MODE != 0) braf = args.bra_feat[item];
@@ -1087,7 +1162,7 @@ jk_class_kernel(const JkClassArgs args)
                 if (threadIdx.x < 32) {
                     bool sig, stop, band;
                     float dmq;
-                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, item, base + lane, ke, sig, stop, band, dmq,
+                    jk_screen<MODE>(args, bra, braf, mol, dmx, dmol, dmol32, item, base + lane, ke, sig, stop, band, dmq,
                                     s_rsm);
                     s_dm[lane] = dmq;
                     const unsigned msk = __ballot_sync(0xffffffffu, sig);

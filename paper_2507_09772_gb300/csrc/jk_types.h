@@ -15,7 +15,9 @@ struct alignas(16) JkPair {
     int a_ao, b_ao;    // molecule-local Cartesian AO offsets
     int a_loc, b_loc;  // molecule-local shell indices (density-max table)
     double Q;          // Schwarz factor sqrt(max |(mu nu|mu nu)|)
-    double Ax, Ay, Az; // centre of shell a
+    float ABxf, AByf, ABzf;  // A - B rounded to FP32 (the FP32 tier reads these, no conversion)
+    int pad0;
+    double pad1;
     double ABx, ABy, ABz;  // A - B (horizontal recurrence)
     float Qf;              // Q rounded to FP32 (the FP32 screening path)
     float padf;

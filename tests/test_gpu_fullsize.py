@@ -158,7 +158,7 @@ def test_highl_cluster_spherical_mixed_sampled_blocks():
     cart = synth.Molecule(coords=mol.coords, shells=mol.shells.copy(), exps=mol.exps, coeffs=mol.coeffs,
                           nao=mol.nao_cart, nao_cart=mol.nao_cart, name="highl-cart")
     cart.shells[:, 5] = 0
-    Dc = np.einsum("ip,npq,jq->nij", C, mol.D, C)
+    Dc = np.stack([C @ d @ C.T for d in mol.D])   # D_cart = C D_sph C^T
     rng = np.random.default_rng(3)
     jb = _near_and_random_pairs(cart, rng, 1, 1, lmax=1)
     kb = _near_and_random_pairs(cart, rng, 1, 1, lmax=1)
