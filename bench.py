@@ -135,6 +135,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
     ap.add_argument("--forms", default="mixed,routed", help="accelerated forms timed against the FP64 build")
     ap.add_argument("--chunk", type=int, default=0, help="candidate kets per work item (0: the library default)")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="library option KEY=VALUE set on the handle before the run (repeatable)")
     ap.add_argument("--chunk-fp64tier", type=int, default=0,
                     help="the same for the FP64 tier of mixed and routed builds (0: the library default)")
     ap.add_argument("--oracle-blocks", type=int, default=8,
@@ -529,6 +531,9 @@ def run_ours(args):
         eng.set_option("chunk", args.chunk)
     if args.chunk_fp64tier:
         eng.set_option("chunk_fp64tier", args.chunk_fp64tier)
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        eng.set_option(k, float(v))
     Ds = [torch.tensor(m.D, dtype=torch.float64, device="cuda") for m in mols]
     Js = [torch.empty_like(d) for d in Ds]
     Ks = [torch.empty_like(d) for d in Ds]
@@ -683,7 +688,8 @@ def run_ours(args):
                        "l2": "flushed before every step (256 MiB write)",
                        "graph": args.graph, "branches": args.branches,
                        "chunk": eng.get_option("chunk"), "chunk_fp64tier": eng.get_option("chunk_fp64tier"),
-                       "screen64": eng.get_option("screen64"),
+                       "screen64": eng.get_option("screen64"), "widen_int": eng.get_option("widen_int"),
+                       "options": args.opt,
                        "parallelism": f"{ws} independent batch(es), one per GPU"},
             "quartets_per_step": quartets / args.steps,
             "prim_quartets_per_step": sum(s["prim_quartets"] for s in stats) / args.steps,

@@ -786,6 +786,7 @@ struct jk_handle {
     double route_cap = 16777216.0;         // list entries over all launches
     int asym64 = 0;                        // FP32 tier: large-T roots and weights in FP64
     int chunk = 64;                        // kets per work item
+    int widen_int = 1;                     // FP32 tier: float-to-double by integer operations
     int chunk_hi = 64;                     // ... for the FP64 tier of mixed and routed builds
     // bounds compared in FP64 (0: in FP32 when the cutoff is >= 1e-30); FP64
     // costs about 2 % of a mixed build of the batched workload
@@ -1613,6 +1614,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             a.rcount = routed ? h->d_rcount + lidx[k] : nullptr;
             a.rcap = routed ? h->rl_cap[lidx[k]] : 0;
             a.asym64 = h->asym64;
+            a.widen_int = h->widen_int;
             a.log_x = logs ? logs->x : nullptr;
             a.log_y = logs ? logs->y : nullptr;
             a.log_n = h->d_logn;
@@ -1674,7 +1676,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         char keyb[160];
         snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d/%d/%d/%a/%d/%d", ndm, with_j, with_k, mode,
                  cutoff, h->tau32, h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0, h->part_index,
-                 h->part_count, h->prim_eps, h->asym64, h->screen64);
+                 h->part_count, h->prim_eps, h->asym64, h->screen64 + 2 * h->widen_int);
         std::string key = keyb;
         char ob[40];
         snprintf(ob, sizeof ob, "/%a", h->omega);
@@ -2083,6 +2085,7 @@ int jk_set_option(jk_handle *h, const char *key, double value)
         h->branches = (int)value;
     }
     else if (k == "asym64") h->asym64 = value != 0;
+    else if (k == "widen_int") h->widen_int = value != 0;
     else if (k == "chunk" || k == "chunk_fp64tier") {
         if (!(value >= 32 && value <= 65536)) return fail(JK_ERR_ARG, "%s must be in [32, 65536]", key);
         const int c0 = k == "chunk" ? (int)value : h->chunk, c1 = k == "chunk" ? h->chunk_hi : (int)value;
@@ -2126,6 +2129,7 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "omega") *value = h->omega;
     else if (k == "part_index") *value = h->part_index;
     else if (k == "asym64") *value = h->asym64;
+    else if (k == "widen_int") *value = h->widen_int;
     else if (k == "chunk") *value = h->chunk;
     else if (k == "chunk_fp64tier") *value = h->chunk_hi;
     else if (k == "screen64") *value = h->screen64;

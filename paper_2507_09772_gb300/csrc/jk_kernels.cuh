@@ -68,7 +68,7 @@ __device__ __forceinline__ void jk_pair_ab(const JkPair &p, float &x, float &y, 
 // integer operations instead: sign, exponent rebiased from 127 to 1023,
 // fraction shifted left by 29; subnormal floats are normalised first. Exact
 // for every float.
-__device__ __forceinline__ double jk_to_f64(double x) { return x; }
+__device__ __forceinline__ double jk_wide(double x, int) { return x; }
 __device__ __forceinline__ double jk_to_f64(float x)
 {
     const unsigned u = __float_as_uint(x);
@@ -88,6 +88,8 @@ __device__ __forceinline__ double jk_to_f64(float x)
     }
     return __longlong_as_double((long long)bits);
 }
+// wi = 0: the conversion instruction instead (for comparison)
+__device__ __forceinline__ double jk_wide(float x, int wi) { return wi ? jk_to_f64(x) : (double)x; }
 __device__ __forceinline__ float jk_rsqrt(float x) { return rsqrtf(x); }
 
 // ----------------------------------------------------- Rys roots, weights
@@ -133,7 +135,7 @@ __device__ __forceinline__ void jk_rys_one(float T, int r, const float *__restri
                                            float &u, float &w, int a64)
 {
     static_assert(RYS32_DEG == 7, "two float4 per function");
-    if (T >= (float)rys32_tmax[N]) {
+    if (T >= rys32_tmaxf[N]) {
         if (a64) {
             // the same limit evaluated in FP64, rounded once to FP32
             const double s = rsqrt((double)T);
@@ -142,10 +144,11 @@ __device__ __forceinline__ void jk_rys_one(float T, int r, const float *__restri
             return;
         }
         // u = x^2 / T, w = w_h / sqrt(T): no cancellation, so FP32 keeps
-        // ~2 ulp; the Gauss-Hermite constants themselves are FP64-derived
+        // ~2 ulp; the Gauss-Hermite constants are FP64-derived, stored
+        // rounded to FP32
         const float s = rsqrtf(T);
-        u = (float)rys_gh[rys_gh_offset[N - 1] + r] * (s * s);
-        w = (float)rys_gh[rys_gh_offset[N - 1] + N + r] * s;
+        u = rys_gh32[rys_gh_offset[N - 1] + r] * (s * s);
+        w = rys_gh32[rys_gh_offset[N - 1] + N + r] * s;
         return;
     }
     int k = min((int)(T * (float)RYS32_INVH), rys32_nint_c[N] - 1);
@@ -651,7 +654,7 @@ template <> __device__ __forceinline__ const float *jk_dens<float>(const JkMol &
 
 template <int FA, int FB, int FC, int FD, int NDM, int DOJ, int DOK, typename R>
 __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f, const JkMol &mol,
-                                            int a0, int b0, int c0, int d0, R (&jab)[NDM][FA][FB])
+                                            int a0, int b0, int c0, int d0, R (&jab)[NDM][FA][FB], int wi)
 {
     const long long nn = (long long)mol.nao * mol.nao;
     const int nao = mol.nao;
@@ -693,7 +696,7 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
             for (int ic = 0; ic < FC; ++ic)
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, jk_to_f64((R)2 * f * jcd[ic][id]));
+                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, jk_wide((R)2 * f * jcd[ic][id], wi));
         }
         if (DOK) {
             R Dbd[FB][FD], Dbc[FB][FC], Dad[FA][FD], Dac[FA][FC];
@@ -745,26 +748,26 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
             for (int ia = 0; ia < FA; ++ia) {
 #pragma unroll
                 for (int ic = 0; ic < FC; ++ic)
-                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, jk_to_f64(f * kac[ia][ic]));
+                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, jk_wide(f * kac[ia][ic], wi));
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, jk_to_f64(f * kad[ia][id]));
+                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, jk_wide(f * kad[ia][id], wi));
             }
 #pragma unroll
             for (int ib = 0; ib < FB; ++ib) {
 #pragma unroll
                 for (int ic = 0; ic < FC; ++ic)
-                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, jk_to_f64(f * kbc[ib][ic]));
+                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, jk_wide(f * kbc[ib][ic], wi));
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, jk_to_f64(f * kbd[ib][id]));
+                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, jk_wide(f * kbd[ib][id], wi));
             }
         }
     }
 }
 
 template <int FA, int FB, int NDM, typename R>
-__device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol &mol, int a0, int b0)
+__device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol &mol, int a0, int b0, int wi)
 {
     const long long nn = (long long)mol.nao * mol.nao;
 #pragma unroll
@@ -774,7 +777,7 @@ __device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol 
 #pragma unroll
             for (int ib = 0; ib < FB; ++ib)
                 if (jab[m][ia][ib] != (R)0)
-                    atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, jk_to_f64(jab[m][ia][ib]));
+                    atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, jk_wide(jab[m][ia][ib], wi));
 }
 
 // Work item t -> bra pair i (binary search in the item prefix) and the ket
@@ -883,8 +886,8 @@ jk_class_kernel(const JkClassArgs args)
                             for (int jj = 0; jj < FB; ++jj) jab[m][i][jj] = (R)0;
                     const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
                     jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
-                                                                 ket.b_ao + gd * FD, jab);
-                    if (DOJ) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+                                                                 ket.b_ao + gd * FD, jab, args.widen_int);
+                    if (DOJ) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0, args.widen_int);
                     if (tg == 0) { ++nq; nprim += np; }
                 }
             }
@@ -1019,7 +1022,7 @@ jk_class_kernel(const JkClassArgs args)
                         if (ket.a == ket.b) f *= (R)0.5;
                         if (args.same_class && myket == item) f *= (R)0.5;
                         jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
-                                                                     ket.b_ao + gd * FD, jab);
+                                                                     ket.b_ao + gd * FD, jab, args.widen_int);
                         if (MODE == 2) {
                             double tm = 0.0;
 #pragma unroll
@@ -1043,7 +1046,7 @@ jk_class_kernel(const JkClassArgs args)
                 }
                 if (last) break;
             }
-            if (DOJ && active) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+            if (DOJ && active) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0, args.widen_int);
             for (int o = 16; o > 0; o >>= 1) nprim += __shfl_xor_sync(0xffffffffu, nprim, o);
             if (lane == 0 && nq) {
                 atomicAdd(args.stats, nq);
@@ -1108,8 +1111,8 @@ jk_class_kernel(const JkClassArgs args)
                             for (int jj = 0; jj < FB; ++jj) jab[m][i][jj] = (R)0;
                     const int a0 = bra.a_ao + ga * FA, b0 = bra.b_ao + gb * FB;
                     jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
-                                                                 ket.b_ao + gd * FD, jab);
-                    if (DOJ) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+                                                                 ket.b_ao + gd * FD, jab, args.widen_int);
+                    if (DOJ) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0, args.widen_int);
                 }
                 if (slab == 0) { ++nq; nprim += np; }
                 // every thread is done with this entry's shared tables
@@ -1193,7 +1196,7 @@ jk_class_kernel(const JkClassArgs args)
                         if (ket.a == ket.b) f *= (R)0.5;
                         if (args.same_class && myket == item) f *= (R)0.5;
                         jk_contract<FA, FB, FC, FD, NDM, DOJ, DOK, R>(T, f, mol, a0, b0, ket.a_ao + gc * FC,
-                                                                     ket.b_ao + gd * FD, jab);
+                                                                     ket.b_ao + gd * FD, jab, args.widen_int);
                     }
                     if (MODE == 2 && X == 1) {   // labels need the whole block's max |T|
                         __shared__ double s_tm[32];
@@ -1219,7 +1222,7 @@ jk_class_kernel(const JkClassArgs args)
                 }
                 if (stop) break;
             }
-            if (DOJ && act) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0);
+            if (DOJ && act) jk_flush_jab<FA, FB, NDM, R>(jab, mol, a0, b0, args.widen_int);
             if (threadIdx.x == 0 && nq && slab == 0) {
                 atomicAdd(args.stats, nq);
                 atomicAdd(args.stats + 1, nprim);

@@ -123,6 +123,9 @@ struct JkClassArgs {
     // 1: the FP32 tier evaluates the large-T (Gauss-Hermite) roots and
     // weights in FP64 and rounds them to FP32
     int asym64;
+    // 1: the FP32 tier widens its contributions to FP64 with integer bit
+    // operations; 0: with the conversion instruction
+    int widen_int;
 };
 
 // Arguments of the Schwarz (diagonal-quartet) launch of one pair class.

@@ -255,6 +255,12 @@ def write_sources(outdir: str) -> dict:
                 + ",".join(str(o) for o in offs[:-1]) + "};\n")
         f.write(f"__device__ __constant__ double rys_gh[{len(flat)}] = {{"
                 + ",".join(_fmt(v) for v in flat) + "};\n")
+        # the same limits and the FP32 table ends rounded to FP32, so that the
+        # FP32 tier reads floats (no FP64 conversion on its path)
+        f.write(f"__device__ __constant__ float rys_gh32[{len(flat)}] = {{"
+                + ",".join(_fmt(float(np.float32(v))) + "f" for v in flat) + "};\n")
+        f.write(f"__device__ __constant__ float rys32_tmaxf[{NMAX + 1}] = {{0.0f,"
+                + ",".join(_fmt(float(np.float32(p['tmax']))) + "f" for p in p32) + "};\n")
     os.replace(os.path.join(outdir, "rys_params.cuh.tmp"), os.path.join(outdir, "rys_params.cuh"))
     return {"fp64_size": int(t64.size), "fp32_size": int(t32.size)}
 
