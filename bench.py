@@ -49,16 +49,22 @@ PEAK_FP32_NOMINAL = 152 * 256 * 2.07e9
 # otherwise the roofline reports traffic null.
 TRAFFIC_SOURCES = ["paper_2507_09772_gb300/csrc/jk_kernels.cuh", "paper_2507_09772_gb300/csrc/jk_types.h",
                    "paper_2507_09772_gb300/csrc/jk_router.cuh"]
-TRAFFIC_SHA = None                   # kernel sources of the capture below
-TRAFFIC_BYTES_PER_QUARTET = {}       # tier (0 FP64, 1 FP32) -> DRAM bytes per significant quartet
+# Capture of commit a5c70c2 (profiles/jk_class_kernel_dram_traffic_batched8.md):
+# FP64 build 1,730,110,720 B read + 3,588,352 B written, FP32 build
+# 1,294,581,504 B read + 28,416 B written, both over 287,529,305 quartets.
+TRAFFIC_SHA = "f7bad00fedd57b74"     # comment-free kernel sources of the capture
+TRAFFIC_BYTES_PER_QUARTET = {0: 1733699072 / 287529305, 1: 1294609920 / 287529305}
 
 
 def sources_sha():
+    """Hash of the kernel sources without their comments (the text the
+    kernels are compiled from)."""
     import hashlib
+    from paper_2507_09772_gb300.build import _strip_comments
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

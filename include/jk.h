@@ -198,9 +198,9 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * result to FP32, instead of evaluating it in FP32),
  * "chunk_fp64tier" (default 512: the same for the FP64 tier of mixed and
  * routed builds, whose kernels keep only the candidates above tau32),
- * "widen_int" (0/1, default 1: the FP32 tier widens its contributions to
- * FP64 for the atomics with integer bit operations; 0 uses the conversion
- * instruction, which runs on the FP64 pipe),
+ * "widen_int" (0/1, default 0: the FP32 tier widens its contributions to
+ * FP64 for the atomics with the conversion instruction, which runs on the
+ * FP64 pipe; 1 builds the FP64 bit pattern with integer operations),
  * "screen64" (0/1, default 1: compare the screening bounds, tier thresholds
  * and the primitive threshold in FP64; 0 compares them in FP32 when the
  * cutoff is >= 1e-30),

@@ -786,7 +786,11 @@ struct jk_handle {
     double route_cap = 16777216.0;         // list entries over all launches
     int asym64 = 0;                        // FP32 tier: large-T roots and weights in FP64
     int chunk = 64;                        // kets per work item
-    int widen_int = 1;                     // FP32 tier: float-to-double by integer operations
+    // FP32 tier: float-to-double by integer operations (1) or by the
+    // conversion instruction (0, measured 11 % faster on the FP32 tier of
+    // the batched workload: the integer sequence costs more issue slots than
+    // the FP64-pipe instruction it replaces)
+    int widen_int = 0;
     int chunk_hi = 64;                     // ... for the FP64 tier of mixed and routed builds
     // bounds compared in FP64 (0: in FP32 when the cutoff is >= 1e-30); FP64
     // costs about 2 % of a mixed build of the batched workload

@@ -63,11 +63,11 @@ __device__ __forceinline__ void jk_pair_ab(const JkPair &p, float &x, float &y, 
 
 // An FP32 tier contribution widened to FP64 for the FP64 atomics into J and
 // K. A float-to-double conversion is an FP64-pipe instruction (1/64 of the
-// FP32 rate on GB300, as costly as the FP32 arithmetic of a whole small
-// quartet), so the FP32 tier builds the IEEE-754 binary64 bit pattern with
-// integer operations instead: sign, exponent rebiased from 127 to 1023,
-// fraction shifted left by 29; subnormal floats are normalised first. Exact
-// for every float.
+// FP32 rate on GB300); the alternative builds the IEEE-754 binary64 bit
+// pattern with integer operations: sign, exponent rebiased from 127 to
+// 1023, fraction shifted left by 29; subnormal floats are normalised first.
+// Exact for every float. (Measured: the integer form is the slower of the
+// two on the batched workload, so the conversion is the default.)
 __device__ __forceinline__ double jk_wide(double x, int) { return x; }
 __device__ __forceinline__ double jk_to_f64(float x)
 {
