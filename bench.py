@@ -141,6 +141,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / routed comparison")
     ap.add_argument("--forms", default="mixed,routed", help="accelerated forms timed against the FP64 build")
     ap.add_argument("--chunk", type=int, default=0, help="candidate kets per work item (0: the library default)")
+    ap.add_argument("--router-margin", type=float, default=0.0,
+                    help="added to the trained router's margin (log10 units; larger releases fewer quartets)")
     ap.add_argument("--opt", action="append", default=[],
                     help="library option KEY=VALUE set on the handle before the run (repeatable)")
     ap.add_argument("--chunk-fp64tier", type=int, default=0,
@@ -485,11 +487,12 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets
         n = min(cap, jk.jk_router_collect(eng_l.h, Dl, 1, args.cutoff, Jl, Kl, X, y))
         eng_l.close()
         blob, tst = jk.jk_router_train(X[:n], y[:n], steps=1500, batch=8192, lr=2e-3, quantile=0.95, seed=1)
+        blob.margin += args.router_margin
         train_s = time.perf_counter() - t0
         eng.load_router(blob)
         r = timed("routed")
         r["tiers"] = tier_split(eng, Ds, Js, Ks, args, "routed")
-        r.update({"train_samples": int(n), "train_s": train_s, "train_loss_first": tst["loss_first"],
+        r.update({"train_samples": int(n), "train_s": train_s, "margin": float(blob.margin), "train_loss_first": tst["loss_first"],
                   "train_loss_last": tst["loss_last"],
                   "train_set": "FP64 labels of 6 held-out batch molecules and a 64-unit cluster"})
         if ref_mixed:
