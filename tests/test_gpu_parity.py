@@ -195,6 +195,24 @@ def test_mixed_precision_within_tolerance():
     assert maxdiff(K, Kr) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("opts", [{"asym64": 1}, {"screen64": 0}, {"widen_int": 1}, {"chunk_fp64tier": 64}])
+def test_mixed_precision_options_within_tolerance(opts):
+    """The precision and scheduling options of a mixed build (FP64 large-T
+    Rys limit, plain FP32 bound compares, integer widening, FP64-tier work
+    items) against the oracle; every option keeps each quartet in exactly
+    one tier, so the quartet counts match the FP64 build (plain FP32
+    compares may flip a quartet within one rounding of the cutoff)."""
+    mol = synth.batched_molecule(2, natm=12)
+    _, _, s64 = gpu_jk(mol, cutoff=1e-13)
+    J, K, st = gpu_jk(mol, cutoff=1e-13, precision="mixed", options=opts)
+    Jr, Kr, _ = oracle.jk(mol, cutoff=1e-13)
+    assert st["quartets_fp32"] > 0 and st["quartets_fp64"] > 0
+    flips = max(4, int(1e-6 * s64["quartets_fp64"])) if "screen64" in opts else 0
+    assert abs(st["quartets_fp64"] + st["quartets_fp32"] - s64["quartets_fp64"]) <= flips
+    assert maxdiff(J, Jr) <= TOL_MIXED
+    assert maxdiff(K, Kr) <= TOL_MIXED
+
+
 def test_fp32_mode_error_is_single_precision_sized():
     mol = synth.tiny_631gs()
     J, K, st = gpu_jk(mol, cutoff=1e-13, precision="fp32")
