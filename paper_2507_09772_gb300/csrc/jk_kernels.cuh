@@ -27,13 +27,6 @@
 
 #define JK_TWO_PI_2_5 34.986836655249725  // 2 pi^(5/2)
 
-// Blocks per SM the class kernels are compiled for (the compiler caps the
-// registers per thread to fit them); 1 leaves the compiler's choice. The
-// library sets it per launch from the option "fp32_minblocks".
-#ifndef JK_MIN_BLOCKS
-#define JK_MIN_BLOCKS 1
-#endif
-
 __device__ constexpr int jk_ncart(int l) { return (l + 1) * (l + 2) / 2; }
 
 // Cartesian exponent along `axis` of component idx of a shell with angular
@@ -810,8 +803,7 @@ __device__ __forceinline__ int jk_item_bra(const JkClassArgs &args, long long t)
 template <int LA, int LB, int LC, int LD, int NPA, int NPB, int NPC, int NPD,
           int GA, int GB, int GC, int GD, int X, int NDM, int DOJ, int DOK, typename R, int MODE, int OP>
 __global__ void __launch_bounds__(JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G <= 32 ? 128
-                                  : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G / X + 31) / 32) * 32,
-                                  JK_MIN_BLOCKS)
+                                  : ((JkShape<LA, LB, LC, LD, GA, GB, GC, GD>::G / X + 31) / 32) * 32)
 jk_class_kernel(const JkClassArgs args)
 {
     typedef JkShape<LA, LB, LC, LD, GA, GB, GC, GD, OP> S;
