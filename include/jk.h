@@ -201,9 +201,6 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * "widen_int" (0/1, default 0: the FP32 tier widens its contributions to
  * FP64 for the atomics with the conversion instruction, which runs on the
  * FP64 pipe; 1 builds the FP64 bit pattern with integer operations),
- * "fp32_maxreg" (0 or 32..255, default 0: a register cap passed to the
- * runtime compiler for the FP32-tier kernels, trading spills for
- * occupancy; 0 leaves the compiler's choice),
  * "screen64" (0/1, default 1: compare the screening bounds, tier thresholds
  * and the primitive threshold in FP64; 0 compares them in FP32 when the
  * cutoff is >= 1e-30),

@@ -119,7 +119,6 @@ struct KSpec {
     int ndm = 1, doj = 1, dok = 1, fp32 = 0;
     int mode = 0;  // 0 plain, 1 routed (learned router in the band), 2 label logging
     int op = 0;    // 0 1/r, 1 erf(w r)/r, 2 erfc(w r)/r
-    int maxreg = 0;  // > 0: NVRTC register cap (--maxrregcount), for occupancy experiments
 
     std::string name() const
     {
@@ -194,9 +193,8 @@ std::vector<std::string> nvrtc_options(const KSpec &s)
 {
     // No --use_fast_math for the FP32 tier: the pair data already hold every
     // exponential, and the router's arithmetic stays exactly rounded.
-    std::vector<std::string> o = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
-    if (s.maxreg > 0) o.push_back("--maxrregcount=" + std::to_string(s.maxreg));
-    return o;
+    (void)s;
+    return {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
 }
 
 uint64_t spec_key(const KSpec &s)
@@ -788,7 +786,6 @@ struct jk_handle {
     double route_cap = 16777216.0;         // list entries over all launches
     int asym64 = 0;                        // FP32 tier: large-T roots and weights in FP64
     int chunk = 64;                        // kets per work item
-    int fp32_maxreg = 0;                   // > 0: register cap of the FP32-tier kernels
     // FP32 tier: float-to-double by integer operations (1) or by the
     // conversion instruction (0, measured 11 % faster on the FP32 tier of
     // the batched workload: the integer sequence costs more issue slots than
@@ -1396,7 +1393,6 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
             s.ndm = ndm; s.doj = with_j ? 1 : 0; s.dok = with_k ? 1 : 0;
             s.mode = logs ? 2 : (routed ? (t == 0 ? 1 : (t == 2 ? 3 : 0)) : 0);
             s.op = h->omega == 0.0 ? 0 : (h->omega > 0.0 ? 1 : 2);
-            if (t > 0) s.maxreg = h->fp32_maxreg;
             specs.push_back(s);
             lidx.push_back((int)i);
             tier.push_back(t);
@@ -1684,7 +1680,7 @@ int build_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, in
         char keyb[160];
         snprintf(keyb, sizeof keyb, "%d/%d/%d/%d/%a/%a/%a/%d/%d/%zu/%d/%d/%d/%a/%d/%d", ndm, with_j, with_k, mode,
                  cutoff, h->tau32, h->router_band, h->use_dmax, nbranch, h->cart_gen, prof ? 1 : 0, h->part_index,
-                 h->part_count, h->prim_eps, h->asym64, h->screen64 + 2 * h->widen_int + 4 * h->fp32_maxreg);
+                 h->part_count, h->prim_eps, h->asym64, h->screen64 + 2 * h->widen_int);
         std::string key = keyb;
         char ob[40];
         snprintf(ob, sizeof ob, "/%a", h->omega);
@@ -1907,7 +1903,6 @@ int tune_impl(jk_handle *h, const double *const *D, int32_t ndm, int with_j, int
             for (auto c : it.c) {
                 c.ndm = ndm; c.doj = with_j ? 1 : 0; c.dok = with_k ? 1 : 0;
                 c.mode = (mode == JK_PREC_MIXED_ROUTED && it.t == 0) ? 1 : 0;
-                if (it.t > 0) c.maxreg = h->fp32_maxreg;
                 c.op = h->omega == 0.0 ? 0 : (h->omega > 0.0 ? 1 : 2);
                 all.push_back(c);
             }
@@ -2095,10 +2090,6 @@ int jk_set_option(jk_handle *h, const char *key, double value)
     }
     else if (k == "asym64") h->asym64 = value != 0;
     else if (k == "widen_int") h->widen_int = value != 0;
-    else if (k == "fp32_maxreg") {
-        if (!(value == 0 || (value >= 32 && value <= 255))) return fail(JK_ERR_ARG, "fp32_maxreg must be 0 or in [32, 255]");
-        h->fp32_maxreg = (int)value;
-    }
     else if (k == "chunk" || k == "chunk_fp64tier") {
         if (!(value >= 32 && value <= 65536)) return fail(JK_ERR_ARG, "%s must be in [32, 65536]", key);
         const int c0 = k == "chunk" ? (int)value : h->chunk, c1 = k == "chunk" ? h->chunk_hi : (int)value;
@@ -2143,7 +2134,6 @@ int jk_get_option(jk_handle *h, const char *key, double *value)
     else if (k == "part_index") *value = h->part_index;
     else if (k == "asym64") *value = h->asym64;
     else if (k == "widen_int") *value = h->widen_int;
-    else if (k == "fp32_maxreg") *value = h->fp32_maxreg;
     else if (k == "chunk") *value = h->chunk;
     else if (k == "chunk_fp64tier") *value = h->chunk_hi;
     else if (k == "screen64") *value = h->screen64;
