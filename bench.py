@@ -49,11 +49,13 @@ PEAK_FP32_NOMINAL = 152 * 256 * 2.07e9
 # otherwise the roofline reports traffic null.
 TRAFFIC_SOURCES = ["paper_2507_09772_gb300/csrc/jk_kernels.cuh", "paper_2507_09772_gb300/csrc/jk_types.h",
                    "paper_2507_09772_gb300/csrc/jk_router.cuh"]
-# Capture of commit a5c70c2 (profiles/jk_class_kernel_dram_traffic_batched8.md):
-# FP64 build 1,730,110,720 B read + 3,588,352 B written, FP32 build
-# 1,294,581,504 B read + 28,416 B written, both over 287,529,305 quartets.
-TRAFFIC_SHA = "f7bad00fedd57b74"     # comment-free kernel sources of the capture
-TRAFFIC_BYTES_PER_QUARTET = {0: 1733699072 / 287529305, 1: 1294609920 / 287529305}
+# Captures of the 8-molecule case (profiles/jk_class_kernel_dram_traffic_batched8.md):
+# FP32 build of the current kernels 1,289,914,624 B read + 0 B written; FP64
+# build 1,715,792,896 B read + 3,408,896 B written, taken on the kernels just
+# before J and K moved from ATOM to RED accumulation (an L2-side change: J
+# and K of these molecules stay in L2); both over 287,529,305 quartets.
+TRAFFIC_SHA = "83e18b6215b51bc2"     # comment-free kernel sources of the FP32 capture
+TRAFFIC_BYTES_PER_QUARTET = {0: 1719201792 / 287529305, 1: 1289914624 / 287529305}
 
 
 def sources_sha():

@@ -652,6 +652,15 @@ template <typename R> __device__ __forceinline__ const R *jk_dens(const JkMol &m
 template <> __device__ __forceinline__ const double *jk_dens<double>(const JkMol &mol) { return mol.D; }
 template <> __device__ __forceinline__ const float *jk_dens<float>(const JkMol &mol) { return mol.D32; }
 
+// J and K accumulate by FP64 reductions that return nothing (RED): atomicAdd
+// on doubles issues ATOM, whose value the L2 sends back although nobody
+// reads it (ncu: 9.7e9 ATOM sectors for one all-FP32 build of 8 molecules,
+// 34 per quartet). Relaxed, device scope: the ordering atomicAdd gives.
+__device__ __forceinline__ void jk_red_add(double *p, double v)
+{
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
 template <int FA, int FB, int FC, int FD, int NDM, int DOJ, int DOK, typename R>
 __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f, const JkMol &mol,
                                             int a0, int b0, int c0, int d0, R (&jab)[NDM][FA][FB], int wi)
@@ -696,7 +705,7 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
             for (int ic = 0; ic < FC; ++ic)
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, jk_wide((R)2 * f * jcd[ic][id], wi));
+                    jk_red_add(mol.J + m * nn + (long long)(c0 + ic) * nao + d0 + id, jk_wide((R)2 * f * jcd[ic][id], wi));
         }
         if (DOK) {
             R Dbd[FB][FD], Dbc[FB][FC], Dad[FA][FD], Dac[FA][FC];
@@ -748,19 +757,19 @@ __device__ __forceinline__ void jk_contract(const R (&T)[FA * FB * FC * FD], R f
             for (int ia = 0; ia < FA; ++ia) {
 #pragma unroll
                 for (int ic = 0; ic < FC; ++ic)
-                    atomicAdd(K + (long long)(a0 + ia) * nao + c0 + ic, jk_wide(f * kac[ia][ic], wi));
+                    jk_red_add(K + (long long)(a0 + ia) * nao + c0 + ic, jk_wide(f * kac[ia][ic], wi));
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(K + (long long)(a0 + ia) * nao + d0 + id, jk_wide(f * kad[ia][id], wi));
+                    jk_red_add(K + (long long)(a0 + ia) * nao + d0 + id, jk_wide(f * kad[ia][id], wi));
             }
 #pragma unroll
             for (int ib = 0; ib < FB; ++ib) {
 #pragma unroll
                 for (int ic = 0; ic < FC; ++ic)
-                    atomicAdd(K + (long long)(b0 + ib) * nao + c0 + ic, jk_wide(f * kbc[ib][ic], wi));
+                    jk_red_add(K + (long long)(b0 + ib) * nao + c0 + ic, jk_wide(f * kbc[ib][ic], wi));
 #pragma unroll
                 for (int id = 0; id < FD; ++id)
-                    atomicAdd(K + (long long)(b0 + ib) * nao + d0 + id, jk_wide(f * kbd[ib][id], wi));
+                    jk_red_add(K + (long long)(b0 + ib) * nao + d0 + id, jk_wide(f * kbd[ib][id], wi));
             }
         }
     }
@@ -777,7 +786,7 @@ __device__ __forceinline__ void jk_flush_jab(R (&jab)[NDM][FA][FB], const JkMol 
 #pragma unroll
             for (int ib = 0; ib < FB; ++ib)
                 if (jab[m][ia][ib] != (R)0)
-                    atomicAdd(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, jk_wide(jab[m][ia][ib], wi));
+                    jk_red_add(mol.J + m * nn + (long long)(a0 + ia) * mol.nao + b0 + ib, jk_wide(jab[m][ia][ib], wi));
 }
 
 // Work item t -> bra pair i (binary search in the item prefix) and the ket
