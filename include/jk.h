@@ -199,11 +199,13 @@ int jk_build_batch(jk_handle *h, const double *const *D, int32_t n_dm, int with_
  * "chunk_fp64tier" (default 512: the same for the FP64 tier of mixed and
  * routed builds, whose kernels keep only the candidates above tau32),
  * "widen_int" (0/1, default 0: the FP32 tier widens its contributions to
- * FP64 for the atomics with the conversion instruction, which runs on the
+ * FP64 for the J/K reductions with the conversion instruction, which runs on the
  * FP64 pipe; 1 builds the FP64 bit pattern with integer operations),
- * "screen64" (0/1, default 1: compare the screening bounds, tier thresholds
- * and the primitive threshold in FP64; 0 compares them in FP32 when the
- * cutoff is >= 1e-30),
+ * "screen64" (0/1, default 1: the screening bounds, tier thresholds and
+ * the primitive threshold decide as FP64 compares would: the compare runs
+ * in FP32 and is redone in FP64 when the two sides are within a relative
+ * 2e-6 of each other; 0 keeps the plain FP32 compare when the cutoff is
+ * >= 1e-30),
  * "route_cap" (default 16777216: initial entries of the per-class-pair lists
  * of quartets the router releases from the FP64 tier, shared out by
  * candidate count; a list that overflowed in a build with stats is grown
