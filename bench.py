@@ -415,8 +415,14 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets
            "tau32": args.tau32, "accuracy_reference": f"the {base} build of this run (full matrices)"}
 
     def timed(precision):
+        # the first build of a form compiles (or loads from the disk cache)
+        # its kernels and captures its graph: timed on the host, apart
+        c0 = eng.get_option("compile_ms")
+        t0 = time.perf_counter()
         _, _, st = eng.build(Ds, cutoff=args.cutoff, precision=precision, J=Js, K=Ks, stats=True)  # warm
         torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        compile_ms = eng.get_option("compile_ms") - c0
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         sts = []
@@ -436,17 +442,21 @@ def run_forms(args, eng, mols, Ds, Js, Ks, flush, stream, base_ms, base_quartets
              "max_abs_dJ": dj, "max_abs_dK": dk, "within_1e-8": bool(max(dj, dk) <= 1e-8),
              "fp32_fraction": st["quartets_fp32"] / max(1, q), "quartets_fp64": st["quartets_fp64"],
              "quartets_fp32": st["quartets_fp32"], "quartets_routed": st["quartets_routed"],
-             f"same_quartets_as_{base}": bool(q == base_quartets)}
+             f"same_quartets_as_{base}": bool(q == base_quartets),
+             "first_build_s": first_s, "compile_ms": compile_ms}
         if ocmp is not None:
             r.update(ocmp(Js[0], Ks[0]))
         return r
 
     if "mixed" in forms:
         # the FP32 tier's shapes, tuned on all-FP32 builds (most mixed quartets are FP32)
+        t0 = time.perf_counter()
         tune = (eng.autotune(Ds, cutoff=args.cutoff, precision="fp32", max_candidates=3, min_share=0.01)
                 if args.tune else None)
+        tune_s = time.perf_counter() - t0
         out["mixed"] = timed("mixed")
         out["mixed"]["autotune"] = tune
+        out["mixed"]["autotune_s"] = tune_s
         out["mixed"]["tiers"] = tier_split(eng, Ds, Js, Ks, args, "mixed")
     # the mixed build with the large-T Rys limit of the FP32 tier in FP64
     # (asym64 = 1), and with the bounds compared in plain FP32 (screen64 = 0)
@@ -552,8 +562,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     tune = None
+    t0 = time.perf_counter()
     if args.tune:
         tune = eng.autotune(Ds, cutoff=args.cutoff, precision=args.precision, max_candidates=3, min_share=0.01)
+    tune_s = time.perf_counter() - t0
 
     def step(stats=True):
         flush.fill_(1)
@@ -563,6 +575,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     first = step()
     first_s = time.perf_counter() - t0
+    first_compile_ms = eng.get_option("compile_ms")
     for _ in range(max(0, args.warmup - 1)):
         step()
     torch.cuda.synchronize()
@@ -718,7 +731,9 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "init_ms": 1e3 * init_s,
             "first_build_s": first_s,
-            "compile_ms": eng.get_option("compile_ms"),
+            "compile_ms": first_compile_ms,
+            "compile_ms_all_forms": eng.get_option("compile_ms"),
+            "autotune_s": tune_s,
             "peak_probe_fp64_tflops": None if args.no_probe else args.probe64 / 1e12,
             "peak_probe_fp32_tflops": None if args.no_probe else args.probe32 / 1e12,
             "top_kernels": sorted(
