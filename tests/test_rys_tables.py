@@ -17,7 +17,7 @@ from paper_2507_09772_gb300 import rys_gen
 
 @pytest.fixture(scope="module")
 def tables():
-    return rys_gen.fit_tables(rys_gen.FP64_FIT, nmax=7)
+    return rys_gen.fit_tables(rys_gen.FP64_FIT, nmax=rys_gen.NMAX)
 
 
 def boys_quad(n, T):
@@ -26,8 +26,8 @@ def boys_quad(n, T):
     return v
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 5, 7])
-@pytest.mark.parametrize("T", [0.0, 0.37, 2.9, 11.2, 27.5, 39.9, 50.2, 80.0, 300.0])
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7, 8, 9])
+@pytest.mark.parametrize("T", [0.0, 0.37, 2.9, 11.2, 27.5, 39.9, 50.2, 80.0, 91.5, 300.0])
 def test_moment_exactness_of_interpolated_rule(tables, N, T):
     tab, params = tables
     u, W = rys_gen.evaluate(tab, params[N - 1], T)
@@ -37,7 +37,7 @@ def test_moment_exactness_of_interpolated_rule(tables, N, T):
         assert got == pytest.approx(ref, rel=5e-13), (N, T, n)
 
 
-@pytest.mark.parametrize("N", range(1, 8))
+@pytest.mark.parametrize("N", range(1, rys_gen.NMAX + 1))
 def test_zero_T_limit_is_gauss_legendre(tables, N):
     tab, params = tables
     u, W = rys_gen.evaluate(tab, params[N - 1], 0.0)
@@ -47,7 +47,7 @@ def test_zero_T_limit_is_gauss_legendre(tables, N):
     assert np.allclose(W[np.argsort(u)], w[pos][np.argsort(x[pos] ** 2)], rtol=1e-13, atol=0)
 
 
-@pytest.mark.parametrize("N", range(1, 8))
+@pytest.mark.parametrize("N", range(1, rys_gen.NMAX + 1))
 def test_large_T_limit_is_gauss_hermite(tables, N):
     tab, params = tables
     T = 500.0
@@ -58,7 +58,7 @@ def test_large_T_limit_is_gauss_hermite(tables, N):
     assert np.allclose(np.sort(W), np.sort(w[pos] / math.sqrt(T)), rtol=1e-13, atol=0)
 
 
-@pytest.mark.parametrize("N", [2, 4, 7])
+@pytest.mark.parametrize("N", [2, 4, 7, 8, 9])
 def test_interpolation_matches_exact_rule_across_intervals(tables, N):
     tab, params = tables
     rng = np.random.default_rng(N)
@@ -70,9 +70,9 @@ def test_interpolation_matches_exact_rule_across_intervals(tables, N):
 
 
 def test_fp32_tables_are_accurate_to_single_precision():
-    tab, params = rys_gen.fit_tables(rys_gen.FP32_FIT, nmax=5)
+    tab, params = rys_gen.fit_tables(rys_gen.FP32_FIT, nmax=rys_gen.NMAX)
     rng = np.random.default_rng(0)
-    for N in range(1, 6):
+    for N in range(1, rys_gen.NMAX + 1):
         for T in rng.uniform(0, params[N - 1]["tmax"], 30):
             ue, We = rys_gen.rys_exact(N, T)
             u, W = rys_gen.evaluate(tab, params[N - 1], T)
@@ -80,7 +80,7 @@ def test_fp32_tables_are_accurate_to_single_precision():
             assert np.max(np.abs(W / We - 1)) < 2e-6
 
 
-@pytest.mark.parametrize("N", [1, 2, 4, 7])
+@pytest.mark.parametrize("N", [1, 2, 4, 7, 9])
 def test_split_precision_evaluation_matches_exact_rule(tables, N):
     """The FP64 tier's layout: FP64 head c0..c5, FP32 tail c6..c9."""
     tab, params = tables
