@@ -45,17 +45,20 @@ PEAK_FP32_NOMINAL = 152 * 256 * 2.07e9
 # build), from one ncu capture of the 8-molecule case of the batched workload
 # (`bench.py --nmol 8 ... --tune 0`, heuristic fragment shapes), per
 # significant quartet of that build, per tier; scaled to a step by its quartet
-# count. Valid only for the kernel sources it was taken with (hash below);
-# otherwise the roofline reports traffic null.
+# count. A capture counts as the traffic of the kernels only while the
+# kernel sources hash to the value it was taken with; otherwise the roofline
+# reports traffic null and gives the capture apart, labelled as earlier.
 TRAFFIC_SOURCES = ["paper_2507_09772_gb300/csrc/jk_kernels.cuh", "paper_2507_09772_gb300/csrc/jk_types.h",
                    "paper_2507_09772_gb300/csrc/jk_router.cuh"]
-# Captures of the 8-molecule case (profiles/jk_class_kernel_dram_traffic_batched8.md):
-# FP32 build of the current kernels 1,289,914,624 B read + 0 B written; FP64
-# build 1,715,792,896 B read + 3,408,896 B written, taken on the kernels just
-# before J and K moved from ATOM to RED accumulation (an L2-side change: J
-# and K of these molecules stay in L2); both over 287,529,305 quartets.
-TRAFFIC_SHA = "83e18b6215b51bc2"     # comment-free kernel sources of the FP32 capture
-TRAFFIC_BYTES_PER_QUARTET = {0: 1719201792 / 287529305, 1: 1289914624 / 287529305}
+# Captures of the 8-molecule case (profiles/jk_class_kernel_dram_traffic_batched8.md),
+# both over 287,529,305 quartets, with the hash of the comment-free kernel
+# sources they ran:
+#   tier 0 (FP64 build): 1,715,792,896 B read + 3,408,896 B written, on the
+#     kernels just before J and K moved from ATOM to RED accumulation;
+#   tier 1 (FP32 build): 1,289,914,624 B read + 0 B written, on the RED
+#     kernels.
+TRAFFIC_CAPTURES = {0: (1719201792 / 287529305, "f7bad00fedd57b74"),
+                    1: (1289914624 / 287529305, "83e18b6215b51bc2")}
 
 
 def sources_sha():
@@ -70,12 +73,17 @@ def sources_sha():
     return h.hexdigest()[:16]
 
 
-def traffic_for(tier, quartets):
-    """DRAM bytes of the class kernels of one tier for `quartets` quartets, or
-    None when no capture of the current kernel sources exists."""
-    if TRAFFIC_SHA is None or tier not in TRAFFIC_BYTES_PER_QUARTET or sources_sha() != TRAFFIC_SHA:
+def traffic_for(tier, quartets, current=True):
+    """DRAM bytes of the class kernels of one tier for `quartets` quartets
+    from its capture, or None when there is none. With current (the
+    default), None also when the kernel sources have changed since the
+    capture."""
+    if tier not in TRAFFIC_CAPTURES:
         return None
-    return TRAFFIC_BYTES_PER_QUARTET[tier] * quartets
+    per_q, sha = TRAFFIC_CAPTURES[tier]
+    if current and sources_sha() != sha:
+        return None
+    return per_q * quartets
 
 
 def family_roofline(prof_rows, tier, probe, ms_serial):
@@ -96,12 +104,18 @@ def family_roofline(prof_rows, tier, probe, ms_serial):
     ach = fl / (ms * 1e-3) if ms > 0 else 0.0
     dom = max(rows, key=lambda v: v["ms"])
     traffic = traffic_for(tier, q)
+    earlier = traffic_for(tier, q, current=False) if traffic is None else None
     return {
         "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
         "traffic": traffic / n if traffic is not None else None,
         "traffic_note": ("DRAM bytes per launch (family average) from an 8-molecule ncu capture, per quartet, "
                          "scaled by this step's quartets: %.1f GB/s over the launches"
                          % (traffic / (ms * 1e-3) / 1e9)) if traffic is not None else None,
+        "traffic_earlier_capture": ({
+            "bytes_per_launch": earlier / n, "kernel_sources": TRAFFIC_CAPTURES[tier][1],
+            "note": "DRAM bytes per launch from an ncu capture of an earlier version of these kernels (sources "
+                    "hash %s, now %s), scaled by this step's quartets; not the traffic of the kernels timed here"
+                    % (TRAFFIC_CAPTURES[tier][1], sources_sha())} if earlier is not None else None),
         "kernel": "jk_class_kernel<..., %s> (all %d class instantiations of the tier)"
                   % ("double" if tier == 0 else "float", n),
         "launches": n, "launch_ms": ms / n, "kernel_ms": ms,

@@ -27,12 +27,27 @@ def test_roofline_traffic_is_null_for_changed_or_unknown_kernels():
     import bench
     assert bench.traffic_for(7, 1000) is None   # no such tier
     # recorded bytes are used only while the kernel sources hash to the capture's value
-    for tier, per_q in bench.TRAFFIC_BYTES_PER_QUARTET.items():
+    for tier, (per_q, sha) in bench.TRAFFIC_CAPTURES.items():
         got = bench.traffic_for(tier, 1000)
-        if bench.sources_sha() == bench.TRAFFIC_SHA:
+        if bench.sources_sha() == sha:
             assert got == per_q * 1000
         else:
             assert got is None
+        assert bench.traffic_for(tier, 1000, current=False) == per_q * 1000
+
+
+def test_family_roofline_reports_an_earlier_capture_apart(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = [dict(la=0, lb=0, lc=0, ld=0, na=1, nb=1, nc=1, nd=1, tier=0, threads_per_quartet=1, regs=64,
+                 ms=2.0, flops_model=2e9, quartets=100, launches=2)]
+    monkeypatch.setattr(bench, "TRAFFIC_CAPTURES", {0: (10.0, "0" * 16)})
+    r = bench.family_roofline(rows, 0, None, 2.0)
+    assert r["traffic"] is None and r["traffic_note"] is None
+    assert r["traffic_earlier_capture"]["bytes_per_launch"] == 500.0
+    monkeypatch.setattr(bench, "TRAFFIC_CAPTURES", {0: (10.0, bench.sources_sha())})
+    r = bench.family_roofline(rows, 0, None, 2.0)
+    assert r["traffic"] == 500.0 and r["traffic_earlier_capture"] is None
 
 
 def test_family_roofline_arithmetic():
